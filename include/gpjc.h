@@ -1,0 +1,209 @@
+/*
+ * gpjc — group-patch joint compression of B0/RF-encoded MRI on one GPU.
+ *
+ * C ABI of the compression and reconstruction hot path of
+ *   R. Tian, K. Scheffler, "Group-Patch Joint Compression: Compressing Dynamic
+ *   B0 and Static RF Spatial Modulations Across k-Space Subregion Groups for
+ *   Highly Accelerated MRI", arXiv 2601.05418.
+ *
+ * Model (Sec. 2.2, Eq. 1-4):   S = E rho,  S[line][coil][t]
+ *   E = M F_pe Psi F_ro C : coil multiply C, centred zero-padded readout DFT
+ *   F_ro (N_tx = os N_x samples), wave phase Psi = exp(-i phi(t,y,z)) with
+ *   phi = 2 pi [a_y(t) y_c/N_y + a_z(t) z_c/N_z], a_y = kappa_y (1-cos th)/2,
+ *   a_z = kappa_z sin(th)/2, th = 2 pi cycles t / N_tx (Eq. 3, sinusoidal G_y,
+ *   cosine G_z), centred phase-encode DFT F_pe and sampled-line gather M.
+ * Compression (Sec. 2.4, Eq. 6-15): the readout is cut into patches of w
+ *   samples; patch p belongs to group g = patch_group[p]; with
+ *   N_s = N_C w and patch vector index i = n w + tau (coil-major),
+ *   P_g = sum_{r in ROI} E_g[r] E_g[r]^H / (E_g[r]^H E_g[r])  (Eq. 7-11),
+ *   P_g = U_g F_g U_g^H  (Eq. 8),  A_g = C_g U_g^H (T (x) I_w)  (Eq. 12),
+ *   S'_{l,p} = A_{g(p)} s_{l,p}  (Eq. 13),  E_c = A E  (Eq. 14-15),
+ *   compressed readout length N'_tx = sum_p keep[g(p)].
+ * Reconstruction (Sec. 3.4): CG on E_c^H E_c x = E_c^H S' (Eq. 16) and FISTA
+ *   with an orthonormal Haar l1 term on the detail bands (Eq. 17 with
+ *   lambda_TV = 0).
+ *
+ * Conventions for every call:
+ *   - complex data are interleaved float pairs (complex64, `float` re, im);
+ *   - "d_" pointers are device memory, "h_" pointers host memory; all of them
+ *     stay owned by the caller, the library never frees caller memory;
+ *   - images are [nz][ny][nx] (x fastest); coil maps [nc][nz][ny][nx];
+ *     raw data [n_lines][nc][ntx]; compressed data [n_lines][ntx_c];
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream); calls are
+ *     asynchronous on it unless stated otherwise;
+ *   - every call returns a gpjc_status; arguments are validated before any
+ *     launch; gpjc_last_error() gives a message for the calling thread.
+ *     Nothing aborts, exits or throws across the ABI.
+ *   - handles are immutable after creation apart from their workspaces: one
+ *     operator (gpjc_op) must not be used by two streams at the same time.
+ */
+#ifndef GPJC_H
+#define GPJC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gpjc_status {
+  GPJC_OK = 0,
+  GPJC_EINVAL = 1,       /* invalid argument or geometry */
+  GPJC_ENOMEM = 2,       /* device or host allocation failed */
+  GPJC_ECUDA = 3,        /* a CUDA runtime call failed */
+  GPJC_ETIMEOUT = 4,     /* a bounded device wait gave up */
+  GPJC_ENONFINITE = 5,   /* a non-finite scalar appeared in a reconstruction */
+  GPJC_EUNSUPPORTED = 6  /* valid request outside what this build implements */
+} gpjc_status;
+
+typedef enum gpjc_precision {
+  GPJC_FP32 = 0, /* FP32 data and FFMA compression */
+  GPJC_BF16 = 1  /* BF16 operands on tensor cores, FP32 accumulation, per-group scale */
+} gpjc_precision;
+
+/* Geometry of one slice or volume.  All arrays are host memory, copied by
+ * gpjc_plan_create.  Requirements: nx, ny even; nz == 1 (2D) or even;
+ * nx, ny, nz products of 2, 3, 5, 7; ntx = os * nx divisible by w;
+ * patch_group[p] in [0, n_groups) for p < ntx / w, every group used;
+ * 1 <= keep[g] <= nc * w; lines unique, sorted by (kz, ky), inside the grid. */
+typedef struct gpjc_geom {
+  int32_t nx, ny, nz, nc, os;
+  int32_t w, n_groups;
+  const int32_t* patch_group; /* [ntx / w] */
+  const int32_t* keep;        /* [n_groups] */
+  int32_t n_lines;
+  const int32_t* line_ky; /* [n_lines] */
+  const int32_t* line_kz; /* [n_lines]; NULL for 2D */
+  double cycles, kappa_y, kappa_z; /* wave: cycles per readout, peak-to-peak excursion in lines */
+} gpjc_geom;
+
+typedef struct gpjc_plan gpjc_plan;     /* geometry + bookkeeping tables */
+typedef struct gpjc_groups gpjc_groups; /* compression matrices A_g      */
+typedef struct gpjc_op gpjc_op;         /* E_c operator + workspaces     */
+
+/* ------------------------------------------------------------------ misc -- */
+const char* gpjc_strerror(gpjc_status s);
+/* Message of the last failing call on this thread ("" if none). */
+const char* gpjc_last_error(void);
+/* Library version string. */
+const char* gpjc_version(void);
+
+/* ------------------------------------------------------------------ plan -- */
+/* Validates the geometry and builds the bookkeeping (patch offsets
+ * off[p] = sum_{q<p} keep[g(q)], N'_tx, first patch of each group,
+ * line map) and the device tables.  Synchronous.  *out is owned by the
+ * caller and released with gpjc_plan_destroy. */
+gpjc_status gpjc_plan_create(const gpjc_geom* geom, gpjc_plan** out);
+void gpjc_plan_destroy(gpjc_plan* plan);
+/* Compressed readout length N'_tx (Eq. 15). */
+gpjc_status gpjc_plan_ntx_c(const gpjc_plan* plan, int32_t* ntx_c);
+/* Host copies of the bookkeeping: any pointer may be NULL.
+ * h_off [ntx/w], h_ref [n_groups] (first patch of each group),
+ * h_line_of [nz*ny] (line index of (kz, ky) or -1). */
+gpjc_status gpjc_plan_tables(const gpjc_plan* plan, int32_t* h_off, int32_t* h_ref, int32_t* h_line_of);
+
+/* ------------------------------------------------------------------ groups -- */
+typedef struct gpjc_build_params {
+  int32_t eig_iters;    /* subspace iterations (0 = default 12)                   */
+  int32_t block;        /* subspace block size b (0 = default: min(N_s, max(2 keep, keep + 16), 96)) */
+  int32_t keep_gram;    /* keep P_g (FP64) for gpjc_groups_gram                    */
+} gpjc_build_params;
+
+/* Builds every group's compression matrix from coil maps and a ROI
+ * (Sec. 2.4 steps 1-2, Eq. 6-12): ROI compaction (raster order, pixels that
+ * no coil sees are dropped), Gram P_g in FP64 from the group's first patch,
+ * leading eigenvectors by FP64 subspace iteration + Rayleigh-Ritz,
+ * A_g = C_g U_g^H (T (x) I_w).
+ *   d_coil  [nc][nz][ny][nx] complex64, device
+ *   d_roi   [nz][ny][nx] uint8 (nonzero = inside), device
+ *   h_T     [nc][nc] complex64 noise-decorrelation matrix (row-major), host, or NULL for identity
+ *   params  may be NULL for defaults
+ * Synchronises `stream` (the ROI size sizes internal buffers).  *out is
+ * released with gpjc_groups_destroy and must not outlive `plan`. */
+gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_coil, const uint8_t* d_roi,
+                              const float* h_T, const gpjc_build_params* params, void* stream,
+                              gpjc_groups** out);
+
+/* Groups from given matrices (e.g. a stored result, or an external
+ * solver): h_A holds A_g row-major [keep_g][N_s] complex64 for g = 0..G-1,
+ * concatenated.  Synchronous. */
+gpjc_status gpjc_groups_from_matrices(const gpjc_plan* plan, const float* h_A, gpjc_groups** out);
+void gpjc_groups_destroy(gpjc_groups* groups);
+
+typedef struct gpjc_groups_info {
+  int64_t roi_pixels;  /* |ROI| used by the Gram                        */
+  int32_t block;       /* Ritz values per group (b)                     */
+  double max_residual; /* max_g max_{k<keep} ||P u - lambda u|| / lambda_0 */
+} gpjc_groups_info;
+gpjc_status gpjc_groups_info_get(const gpjc_groups* groups, gpjc_groups_info* info);
+/* h_A: as gpjc_groups_from_matrices.  h_ritz: [n_groups][block] Ritz values,
+ * descending (NULL allowed).  Synchronous. */
+gpjc_status gpjc_groups_get(const gpjc_groups* groups, float* h_A, double* h_ritz);
+/* h_P: [n_groups][N_s][N_s] complex128 Gram matrices (needs keep_gram). */
+gpjc_status gpjc_groups_gram(const gpjc_groups* groups, double* h_P);
+/* h_pix: [roi_pixels] raster indices of the ROI pixels used. */
+gpjc_status gpjc_groups_roi(const gpjc_groups* groups, int32_t* h_pix);
+
+/* ------------------------------------------------------------------ compress -- */
+/* S'_{l,p} = A_{g(p)} s_{l,p} for every line and patch (Eq. 13).
+ *   d_S  [n_lines][nc][ntx] complex64 raw data, device
+ *   d_Sc [n_lines][ntx_c]  complex64 output, device */
+gpjc_status gpjc_compress(const gpjc_groups* groups, const float* d_S, float* d_Sc, gpjc_precision prec,
+                          void* stream);
+
+/* ------------------------------------------------------------------ operator -- */
+/* Binds groups and coil maps (d_coil is referenced, not copied: it must stay
+ * valid and unchanged while the operator lives) and allocates the
+ * workspaces.  nchunk: coil chunks of the readout stage (0 = automatic).
+ * Synchronous. */
+gpjc_status gpjc_op_create(const gpjc_groups* groups, const float* d_coil, gpjc_precision prec, int32_t nchunk,
+                           gpjc_op** out);
+void gpjc_op_destroy(gpjc_op* op);
+/* Times the readout-stage coil-chunk choices on `stream` and keeps the
+ * fastest (synchronous); *nchunk receives it (may be NULL). */
+gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchunk);
+
+/* y = E_c x (Eq. 15): d_x [nz][ny][nx] -> d_y [n_lines][ntx_c]. */
+gpjc_status gpjc_apply_E(const gpjc_op* op, const float* d_x, float* d_y, void* stream);
+/* x = E_c^H y: d_y [n_lines][ntx_c] -> d_x [nz][ny][nx]. */
+gpjc_status gpjc_apply_EH(const gpjc_op* op, const float* d_y, float* d_x, void* stream);
+/* x_out = E_c^H E_c x_in; if h_or_d_qq is non-NULL (device double) it receives ||E_c x_in||^2. */
+gpjc_status gpjc_apply_normal(const gpjc_op* op, const float* d_x, float* d_out, double* d_qq, void* stream);
+
+/* Uncompressed acquisition model (Eq. 4), for simulation and baselines:
+ * d_S [n_lines][nc][ntx] = E d_x, and its adjoint. */
+gpjc_status gpjc_simulate(const gpjc_op* op, const float* d_x, float* d_S, void* stream);
+gpjc_status gpjc_simulate_adjoint(const gpjc_op* op, const float* d_S, float* d_x, void* stream);
+
+/* ------------------------------------------------------------------ recon -- */
+typedef enum gpjc_alg { GPJC_CG = 0, GPJC_FISTA = 1 } gpjc_alg;
+
+typedef struct gpjc_recon_params {
+  int32_t alg;          /* gpjc_alg                                                  */
+  int32_t iters;        /* CG / FISTA iterations (exactly this many)                 */
+  double lambda;        /* FISTA: l1 weight on Haar detail coefficients             */
+  double lipschitz;     /* FISTA: step 1/L; <= 0 => power iteration from E_c^H S'   */
+  int32_t power_iters;  /* power iterations when lipschitz <= 0 (0 = 20)             */
+  int32_t haar_levels;  /* FISTA: Haar levels J (nx, ny divisible by 2^J, J <= 5)   */
+  int32_t use_x0;       /* nonzero: d_x holds the starting image                     */
+  int32_t use_graph;    /* nonzero: capture the iteration loop in a CUDA graph      */
+} gpjc_recon_params;
+
+typedef struct gpjc_recon_info {
+  int32_t status;      /* gpjc_status of the device-side checks                   */
+  double lipschitz;    /* L used by FISTA                                          */
+  double* h_history;   /* optional host [iters + 1]: CG ||r||^2 per iteration      */
+} gpjc_recon_info;
+
+/* Compressed reconstruction of d_Sc [n_lines][ntx_c] into d_x [nz][ny][nx]
+ * (CG-SENSE or FISTA l1-Haar).  The loop runs on the device without host
+ * synchronisation; the call synchronises `stream` once at the end when
+ * `info` is non-NULL (to report status, L and history). */
+gpjc_status gpjc_recon(const gpjc_op* op, const float* d_Sc, float* d_x, const gpjc_recon_params* params,
+                       gpjc_recon_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPJC_H */

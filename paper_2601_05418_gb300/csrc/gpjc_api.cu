@@ -1,0 +1,821 @@
+// Host side of the C ABI declared in include/gpjc.h: validation, the
+// bookkeeping of Sec. 2.3-2.4 (patch offsets, compressed readout length
+// N'_tx = sum_p keep[g(p)] of Eq. 15, first patch of each group), handle
+// lifetimes, workspaces and the launch sequences of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "gpjc.h"
+#include "gpjc_internal.h"
+#include "gpjc_kernels.h"
+
+using namespace gpjc;
+
+// ------------------------------------------------------------------ errors --
+static thread_local std::string g_err;
+
+static gpjc_status fail(gpjc_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+#define CK(call)                                                                         \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess) return fail(GPJC_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" const char* gpjc_strerror(gpjc_status s) {
+  switch (s) {
+    case GPJC_OK: return "ok";
+    case GPJC_EINVAL: return "invalid argument";
+    case GPJC_ENOMEM: return "out of memory";
+    case GPJC_ECUDA: return "CUDA error";
+    case GPJC_ETIMEOUT: return "device wait timed out";
+    case GPJC_ENONFINITE: return "non-finite value in reconstruction";
+    case GPJC_EUNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+extern "C" const char* gpjc_last_error(void) { return g_err.c_str(); }
+extern "C" const char* gpjc_version(void) { return "gpjc 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------------ memory --
+namespace {
+
+struct DevMem {
+  std::vector<void*> ptrs;
+  ~DevMem() { release(); }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+  template <typename T>
+  gpjc_status alloc(T** out, size_t n) {
+    *out = nullptr;
+    if (n == 0) n = 1;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(GPJC_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+    }
+    ptrs.push_back(p);
+    *out = (T*)p;
+    return GPJC_OK;
+  }
+  template <typename T>
+  gpjc_status upload(T** out, const std::vector<T>& v) {
+    gpjc_status s = alloc(out, v.size());
+    if (s) return s;
+    if (!v.empty()) {
+      cudaError_t e = cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return fail(GPJC_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    return GPJC_OK;
+  }
+};
+
+bool factor_fft(int n, FftPlan* pl) {
+  pl->n = n;
+  pl->nst = 0;
+  if (n == 1) return true;
+  int m = n;
+  std::vector<int> r;
+  while (m % 8 == 0) { r.push_back(8); m /= 8; }
+  while (m % 4 == 0) { r.push_back(4); m /= 4; }
+  while (m % 2 == 0) { r.push_back(2); m /= 2; }
+  while (m % 7 == 0) { r.push_back(7); m /= 7; }
+  while (m % 5 == 0) { r.push_back(5); m /= 5; }
+  while (m % 3 == 0) { r.push_back(3); m /= 3; }
+  if (m != 1 || (int)r.size() > kMaxStages) return false;
+  pl->nst = (int)r.size();
+  for (int i = 0; i < pl->nst; ++i) pl->rad[i] = r[i];
+  return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan --
+struct gpjc_plan {
+  int nx, ny, nz, nc, os, ntx, w, G, np, ns, ntxc, n_lines, keep_max;
+  double cycles, kappa_y, kappa_z;
+  std::vector<int> pg, keep, poff, ref, aoff, line_ky, line_kz, line_of;
+  std::vector<int> out_tbase, out_abase, out_astride;
+  Geo geo;
+  DevMem mem;
+};
+
+extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
+  if (!gm || !out) return fail(GPJC_EINVAL, "null geometry or output pointer");
+  *out = nullptr;
+  const int nx = gm->nx, ny = gm->ny, nz = gm->nz, nc = gm->nc, os = gm->os, w = gm->w, G = gm->n_groups;
+  if (nx < 2 || ny < 2 || (nx & 1) || (ny & 1)) return fail(GPJC_EINVAL, "nx, ny must be even and >= 2");
+  if (nz < 1 || (nz > 1 && (nz & 1))) return fail(GPJC_EINVAL, "nz must be 1 or even");
+  if (nc < 1 || nc > 64) return fail(GPJC_EINVAL, "nc must be in [1, 64]");
+  if (os < 1 || os > 16) return fail(GPJC_EINVAL, "os must be in [1, 16]");
+  const long long ntx = (long long)os * nx;
+  if (w < 1 || ntx % w) return fail(GPJC_EINVAL, "w must divide ntx = os*nx");
+  if (G < 1) return fail(GPJC_EINVAL, "n_groups must be >= 1");
+  if (!gm->patch_group || !gm->keep) return fail(GPJC_EINVAL, "patch_group and keep are required");
+  if (gm->n_lines < 1 || !gm->line_ky) return fail(GPJC_EINVAL, "at least one sampled line is required");
+  if (!std::isfinite(gm->cycles) || !std::isfinite(gm->kappa_y) || !std::isfinite(gm->kappa_z))
+    return fail(GPJC_EINVAL, "wave parameters must be finite");
+  FftPlan fx, fy, fz;
+  if (!factor_fft(nx, &fx) || !factor_fft(ny, &fy) || !factor_fft(nz, &fz))
+    return fail(GPJC_EINVAL, "nx, ny, nz must be products of 2, 3, 5, 7");
+  auto* p = new (std::nothrow) gpjc_plan();
+  if (!p) return fail(GPJC_ENOMEM, "host allocation");
+  std::unique_ptr<gpjc_plan> guard(p);
+  p->nx = nx; p->ny = ny; p->nz = nz; p->nc = nc; p->os = os; p->ntx = (int)ntx; p->w = w; p->G = G;
+  p->np = (int)(ntx / w);
+  p->ns = nc * w;
+  p->cycles = gm->cycles; p->kappa_y = gm->kappa_y; p->kappa_z = gm->kappa_z;
+  p->pg.assign(gm->patch_group, gm->patch_group + p->np);
+  p->keep.assign(gm->keep, gm->keep + G);
+  std::vector<int> used(G, 0);
+  for (int q = 0; q < p->np; ++q) {
+    const int g = p->pg[q];
+    if (g < 0 || g >= G) return fail(GPJC_EINVAL, "patch_group[%d] = %d out of range", q, g);
+    used[g] = 1;
+  }
+  p->keep_max = 0;
+  for (int g = 0; g < G; ++g) {
+    if (!used[g]) return fail(GPJC_EINVAL, "group %d has no patch", g);
+    if (p->keep[g] < 1 || p->keep[g] > p->ns) return fail(GPJC_EINVAL, "keep[%d] = %d not in [1, N_s]", g, p->keep[g]);
+    p->keep_max = std::max(p->keep_max, p->keep[g]);
+  }
+  // offsets, compressed length, first patch of each group
+  p->poff.resize(p->np);
+  p->ref.assign(G, -1);
+  long long acc = 0;
+  for (int q = 0; q < p->np; ++q) {
+    p->poff[q] = (int)acc;
+    acc += p->keep[p->pg[q]];
+    if (p->ref[p->pg[q]] < 0) p->ref[p->pg[q]] = q;
+  }
+  if (acc > (1 << 24)) return fail(GPJC_EUNSUPPORTED, "compressed readout too long");
+  p->ntxc = (int)acc;
+  p->aoff.resize(G);
+  long long ao = 0;
+  for (int g = 0; g < G; ++g) {
+    p->aoff[g] = (int)ao;
+    ao += (long long)p->ns * p->keep[g];
+  }
+  if (ao > (1LL << 30)) return fail(GPJC_EUNSUPPORTED, "compression matrices too large");
+  p->out_tbase.resize(p->ntxc);
+  p->out_abase.resize(p->ntxc);
+  p->out_astride.resize(p->ntxc);
+  for (int q = 0; q < p->np; ++q) {
+    const int g = p->pg[q];
+    for (int k = 0; k < p->keep[g]; ++k) {
+      const int o = p->poff[q] + k;
+      p->out_tbase[o] = q * w;
+      p->out_abase[o] = p->aoff[g] + k;
+      p->out_astride[o] = p->keep[g];
+    }
+  }
+  // lines
+  p->n_lines = gm->n_lines;
+  p->line_ky.assign(gm->line_ky, gm->line_ky + gm->n_lines);
+  if (gm->line_kz)
+    p->line_kz.assign(gm->line_kz, gm->line_kz + gm->n_lines);
+  else
+    p->line_kz.assign(gm->n_lines, 0);
+  p->line_of.assign((size_t)nz * ny, -1);
+  for (int l = 0; l < p->n_lines; ++l) {
+    const int ky = p->line_ky[l], kz = p->line_kz[l];
+    if (ky < 0 || ky >= ny || kz < 0 || kz >= nz) return fail(GPJC_EINVAL, "line %d = (%d, %d) outside the grid", l, kz, ky);
+    if (l > 0) {
+      const long long prev = (long long)p->line_kz[l - 1] * ny + p->line_ky[l - 1];
+      const long long cur = (long long)kz * ny + ky;
+      if (cur <= prev) return fail(GPJC_EINVAL, "lines must be unique and sorted by (kz, ky) (line %d)", l);
+    }
+    p->line_of[(size_t)kz * ny + ky] = l;
+  }
+  // resource limits of this build
+  Geo& g = p->geo;
+  memset(&g, 0, sizeof g);
+  g.nx = nx; g.ny = ny; g.nz = nz; g.nc = nc; g.os = os; g.ntx = (int)ntx; g.w = w; g.G = G; g.ns = p->ns;
+  g.np = p->np; g.ntxc = p->ntxc; g.rows = ny * nz; g.n_lines = p->n_lines; g.keep_max = p->keep_max;
+  g.dim3d = nz > 1;
+  g.inv_sqrt_ntx = (float)(1.0 / std::sqrt((double)ntx));
+  g.inv_sqrt_ny = (float)(1.0 / std::sqrt((double)ny));
+  g.inv_sqrt_nz = (float)(1.0 / std::sqrt((double)nz));
+  g.fx = fx; g.fy = fy; g.fz = fz;
+  const size_t k1adj = k1_smem_bytes(g) + sizeof(float2) * (size_t)g.ntxc;
+  if (k1adj > 220 * 1024) return fail(GPJC_EUNSUPPORTED, "readout too long for the shared-memory readout stage");
+  if (g.ntxc > 32 * 256) return fail(GPJC_EUNSUPPORTED, "compressed readout longer than 8192");
+  if (nx > 512) return fail(GPJC_EUNSUPPORTED, "nx > 512");
+  if (ny > 2048 || nz > 2048) return fail(GPJC_EUNSUPPORTED, "phase-encode size > 2048");
+  if (w > 64) return fail(GPJC_EUNSUPPORTED, "w > 64");
+  // device tables
+  DevMem& m = p->mem;
+  int *d_pg, *d_poff, *d_keep, *d_aoff, *d_tb, *d_ab, *d_as, *d_ky, *d_kz, *d_lof;
+  gpjc_status s;
+  if ((s = m.upload(&d_pg, p->pg)) || (s = m.upload(&d_poff, p->poff)) || (s = m.upload(&d_keep, p->keep)) ||
+      (s = m.upload(&d_aoff, p->aoff)) || (s = m.upload(&d_tb, p->out_tbase)) ||
+      (s = m.upload(&d_ab, p->out_abase)) || (s = m.upload(&d_as, p->out_astride)) ||
+      (s = m.upload(&d_ky, p->line_ky)) || (s = m.upload(&d_kz, p->line_kz)) ||
+      (s = m.upload(&d_lof, p->line_of)))
+    return s;
+  float2 *tw_x, *tw_y, *tw_z, *pre;
+  float *ay, *az;
+  if ((s = m.alloc(&tw_x, nx)) || (s = m.alloc(&tw_y, ny)) || (s = m.alloc(&tw_z, nz)) ||
+      (s = m.alloc(&pre, (size_t)ntx)) || (s = m.alloc(&ay, (size_t)ntx)) || (s = m.alloc(&az, (size_t)ntx)))
+    return s;
+  g.pg = d_pg; g.poff = d_poff; g.keep = d_keep; g.aoff = d_aoff; g.out_tbase = d_tb; g.out_abase = d_ab;
+  g.out_astride = d_as; g.line_ky = d_ky; g.line_kz = d_kz; g.line_of = d_lof; g.ay = ay; g.az = az;
+  g.tw_x = tw_x; g.tw_y = tw_y; g.tw_z = tw_z; g.pre = pre;
+  CK(launch_make_tables(g, tw_x, tw_y, tw_z, pre, ay, az, p->cycles, p->kappa_y, p->kappa_z, 0));
+  CK(cudaDeviceSynchronize());
+  *out = guard.release();
+  return GPJC_OK;
+}
+
+extern "C" void gpjc_plan_destroy(gpjc_plan* plan) { delete plan; }
+
+extern "C" gpjc_status gpjc_plan_ntx_c(const gpjc_plan* plan, int32_t* ntx_c) {
+  if (!plan || !ntx_c) return fail(GPJC_EINVAL, "null argument");
+  *ntx_c = plan->ntxc;
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_plan_tables(const gpjc_plan* plan, int32_t* h_off, int32_t* h_ref, int32_t* h_line_of) {
+  if (!plan) return fail(GPJC_EINVAL, "null plan");
+  if (h_off) std::copy(plan->poff.begin(), plan->poff.end(), h_off);
+  if (h_ref) std::copy(plan->ref.begin(), plan->ref.end(), h_ref);
+  if (h_line_of) std::copy(plan->line_of.begin(), plan->line_of.end(), h_line_of);
+  return GPJC_OK;
+}
+
+// ------------------------------------------------------------------ groups --
+struct gpjc_groups {
+  const gpjc_plan* plan;
+  float2* A;        // [aoff[g] + k ns + i]
+  float2* AT;       // [aoff[g] + i keep_g + k]
+  float* scale;     // [G]
+  int* pix;         // [K]
+  double2* P;       // optional [G][ns][ns]
+  long long K;
+  int b;
+  std::vector<double> ritz;  // [G][b]
+  double max_resid;
+  DevMem mem;
+};
+
+static gpjc_status groups_alloc_A(gpjc_groups* gr) {
+  const gpjc_plan* p = gr->plan;
+  const size_t na = (size_t)p->aoff.back() + (size_t)p->ns * p->keep.back();
+  gpjc_status s;
+  if ((s = gr->mem.alloc(&gr->A, na)) || (s = gr->mem.alloc(&gr->AT, na)) || (s = gr->mem.alloc(&gr->scale, p->G)))
+    return s;
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_coil, const uint8_t* d_roi,
+                                         const float* h_T, const gpjc_build_params* params, void* stream,
+                                         gpjc_groups** out) {
+  if (!plan || !d_coil || !d_roi || !out) return fail(GPJC_EINVAL, "null argument");
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Geo& g = plan->geo;
+  gpjc_build_params bp = {0, 0, 0};
+  if (params) bp = *params;
+  const int iters = bp.eig_iters > 0 ? bp.eig_iters : 12;
+  int b = bp.block;
+  if (b <= 0) b = std::min(plan->ns, std::min(96, std::max(2 * plan->keep_max, plan->keep_max + 16)));
+  if (b < plan->keep_max || b > plan->ns) return fail(GPJC_EINVAL, "block %d must be in [keep_max, N_s]", b);
+  if (b > 96) return fail(GPJC_EUNSUPPORTED, "subspace block > 96 (keep too large)");
+  auto* gr = new (std::nothrow) gpjc_groups();
+  if (!gr) return fail(GPJC_ENOMEM, "host allocation");
+  std::unique_ptr<gpjc_groups> guard(gr);
+  gr->plan = plan;
+  gr->b = b;
+  gpjc_status s;
+  if ((s = groups_alloc_A(gr))) return s;
+  DevMem tmp;
+  const size_t L = (size_t)g.rows * g.nx;
+  const int bp_pix = roi_block_pixels();
+  const int nblk = (int)((L + bp_pix - 1) / bp_pix);
+  int *blockcount, *blockoff, *total, *pix;
+  if ((s = tmp.alloc(&blockcount, nblk)) || (s = tmp.alloc(&blockoff, nblk)) || (s = tmp.alloc(&total, 1)) ||
+      (s = gr->mem.alloc(&pix, L)))
+    return s;
+  gr->pix = pix;
+  const float2* coil = (const float2*)d_coil;
+  CK(launch_roi_count(g, coil, d_roi, blockcount, nblk, st));
+  CK(launch_roi_scan(blockcount, blockoff, nblk, total, st));
+  CK(launch_roi_compact(g, coil, d_roi, blockoff, pix, nblk, st));
+  int K = 0;
+  CK(cudaMemcpyAsync(&K, total, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (K <= 0) return fail(GPJC_EINVAL, "ROI is empty (or no coil sees it)");
+  gr->K = K;
+  const int Kpad = ((K + 31) / 32) * 32;
+  float2 *chat, *dT = nullptr;
+  if ((s = tmp.alloc(&chat, (size_t)g.nc * Kpad))) return s;
+  if (h_T) {
+    if ((s = tmp.alloc(&dT, (size_t)g.nc * g.nc))) return s;
+    CK(cudaMemcpyAsync(dT, h_T, sizeof(float2) * g.nc * g.nc, cudaMemcpyHostToDevice, st));
+  }
+  CK(launch_roi_coils(g, coil, dT, pix, K, Kpad, chat, st));
+  // Gram
+  double2* P;
+  DevMem& pm = bp.keep_gram ? gr->mem : tmp;
+  if ((s = pm.alloc(&P, (size_t)g.G * g.ns * g.ns))) return s;
+  CK(cudaMemsetAsync(P, 0, sizeof(double2) * (size_t)g.G * g.ns * g.ns, st));
+  int* d_ref;
+  {
+    std::vector<int> ref(plan->ref.begin(), plan->ref.end());
+    if ((s = tmp.alloc(&d_ref, ref.size()))) return s;
+    CK(cudaMemcpyAsync(d_ref, ref.data(), sizeof(int) * ref.size(), cudaMemcpyHostToDevice, st));
+    CK(launch_gram(g, chat, pix, K, Kpad, d_ref, P, st));
+    CK(launch_hermitize(g, P, st));
+    CK(cudaStreamSynchronize(st));  // ref vector leaves scope
+  }
+  if (bp.keep_gram) gr->P = P;
+  // subspace iteration
+  const size_t nb = (size_t)g.G * g.ns * b;
+  double2 *X, *Y, *Hm, *W, *U;
+  double *ritz, *resid;
+  int* order;
+  if ((s = tmp.alloc(&X, nb)) || (s = tmp.alloc(&Y, nb)) || (s = tmp.alloc(&U, nb)) ||
+      (s = tmp.alloc(&Hm, (size_t)g.G * b * b)) || (s = tmp.alloc(&W, (size_t)g.G * b * b)) ||
+      (s = tmp.alloc(&ritz, (size_t)g.G * b)) || (s = tmp.alloc(&order, (size_t)g.G * b)) ||
+      (s = tmp.alloc(&resid, (size_t)g.G)))
+    return s;
+  CK(launch_eig_init(g, b, X, st));
+  for (int it = 0; it < iters; ++it) {
+    CK(launch_eig_matmul(g, b, P, X, Y, st));
+    CK(launch_eig_orth(g, b, Y, st));
+    std::swap(X, Y);
+  }
+  CK(launch_eig_matmul(g, b, P, X, Y, st));        // Z = P Q
+  CK(launch_eig_project(g, b, X, Y, Hm, st));      // Q^H P Q
+  CK(launch_eig_jacobi(g, b, Hm, W, ritz, order, 60, st));
+  CK(launch_eig_rotate(g, b, X, W, order, U, st)); // Ritz vectors, descending
+  CK(launch_eig_matmul(g, b, P, U, Y, st));        // P U
+  CK(launch_eig_residual(g, b, Y, U, ritz, order, resid, st));
+  CK(launch_form_A(g, b, U, dT, gr->A, gr->AT, gr->scale, st));
+  std::vector<double> rz((size_t)g.G * b), rs(g.G);
+  std::vector<int> ord((size_t)g.G * b);
+  CK(cudaMemcpyAsync(rz.data(), ritz, sizeof(double) * rz.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(ord.data(), order, sizeof(int) * ord.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(rs.data(), resid, sizeof(double) * rs.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  gr->ritz.resize(rz.size());
+  for (int gg = 0; gg < g.G; ++gg)
+    for (int r = 0; r < b; ++r) gr->ritz[(size_t)gg * b + r] = rz[(size_t)gg * b + ord[(size_t)gg * b + r]];
+  gr->max_resid = 0.0;
+  for (double v : rs) gr->max_resid = std::max(gr->max_resid, v);
+  *out = guard.release();
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_groups_from_matrices(const gpjc_plan* plan, const float* h_A, gpjc_groups** out) {
+  if (!plan || !h_A || !out) return fail(GPJC_EINVAL, "null argument");
+  *out = nullptr;
+  auto* gr = new (std::nothrow) gpjc_groups();
+  if (!gr) return fail(GPJC_ENOMEM, "host allocation");
+  std::unique_ptr<gpjc_groups> guard(gr);
+  gr->plan = plan;
+  gr->b = 0;
+  gr->K = 0;
+  gr->max_resid = 0.0;
+  gpjc_status s;
+  if ((s = groups_alloc_A(gr))) return s;
+  const size_t na = (size_t)plan->aoff.back() + (size_t)plan->ns * plan->keep.back();
+  std::vector<float2> hA(na), hAT(na);
+  memcpy(hA.data(), h_A, sizeof(float2) * na);
+  std::vector<float> sc(plan->G, 0.f);
+  for (int g = 0; g < plan->G; ++g) {
+    const int kg = plan->keep[g];
+    for (int k = 0; k < kg; ++k)
+      for (int i = 0; i < plan->ns; ++i) {
+        const float2 v = hA[plan->aoff[g] + (size_t)k * plan->ns + i];
+        if (!std::isfinite(v.x) || !std::isfinite(v.y)) return fail(GPJC_EINVAL, "non-finite A entry (group %d)", g);
+        hAT[plan->aoff[g] + (size_t)i * kg + k] = v;
+        sc[g] = std::max(sc[g], std::max(std::fabs(v.x), std::fabs(v.y)));
+      }
+  }
+  CK(cudaMemcpy(gr->A, hA.data(), sizeof(float2) * na, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(gr->AT, hAT.data(), sizeof(float2) * na, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(gr->scale, sc.data(), sizeof(float) * sc.size(), cudaMemcpyHostToDevice));
+  *out = guard.release();
+  return GPJC_OK;
+}
+
+extern "C" void gpjc_groups_destroy(gpjc_groups* groups) { delete groups; }
+
+extern "C" gpjc_status gpjc_groups_info_get(const gpjc_groups* gr, gpjc_groups_info* info) {
+  if (!gr || !info) return fail(GPJC_EINVAL, "null argument");
+  info->roi_pixels = gr->K;
+  info->block = gr->b;
+  info->max_residual = gr->max_resid;
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_groups_get(const gpjc_groups* gr, float* h_A, double* h_ritz) {
+  if (!gr) return fail(GPJC_EINVAL, "null groups");
+  const gpjc_plan* p = gr->plan;
+  const size_t na = (size_t)p->aoff.back() + (size_t)p->ns * p->keep.back();
+  if (h_A) CK(cudaMemcpy(h_A, gr->A, sizeof(float2) * na, cudaMemcpyDeviceToHost));
+  if (h_ritz && !gr->ritz.empty()) std::copy(gr->ritz.begin(), gr->ritz.end(), h_ritz);
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_groups_gram(const gpjc_groups* gr, double* h_P) {
+  if (!gr || !h_P) return fail(GPJC_EINVAL, "null argument");
+  if (!gr->P) return fail(GPJC_EINVAL, "groups were built without keep_gram");
+  const gpjc_plan* p = gr->plan;
+  CK(cudaMemcpy(h_P, gr->P, sizeof(double2) * (size_t)p->G * p->ns * p->ns, cudaMemcpyDeviceToHost));
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_groups_roi(const gpjc_groups* gr, int32_t* h_pix) {
+  if (!gr || !h_pix) return fail(GPJC_EINVAL, "null argument");
+  if (gr->K <= 0) return fail(GPJC_EINVAL, "groups were not built from a ROI");
+  CK(cudaMemcpy(h_pix, gr->pix, sizeof(int) * (size_t)gr->K, cudaMemcpyDeviceToHost));
+  return GPJC_OK;
+}
+
+// ------------------------------------------------------------------ compress --
+extern "C" gpjc_status gpjc_compress(const gpjc_groups* gr, const float* d_S, float* d_Sc, gpjc_precision prec,
+                                     void* stream) {
+  if (!gr || !d_S || !d_Sc) return fail(GPJC_EINVAL, "null argument");
+  if (prec != GPJC_FP32) return fail(GPJC_EUNSUPPORTED, "this entry point handles FP32; see gpjc_compress_bf16");
+  const Geo& g = gr->plan->geo;
+  CK(launch_compress_fp32(g, (const float2*)d_S, g.n_lines, gr->AT, (float2*)d_Sc, (cudaStream_t)stream));
+  return GPJC_OK;
+}
+
+// ------------------------------------------------------------------ operator --
+enum { SC_BB = 0, SC_QQ = 1, SC_RR0 = 2, SC_RR1 = 3, SC_NV = 4, SC_LIP = 5, SC_TMP = 6, SC_N = 16 };
+
+struct gpjc_op {
+  const gpjc_groups* gr;
+  const gpjc_plan* plan;
+  const float2* coil;
+  gpjc_precision prec;
+  int nchunk, nchunk_max;
+  size_t L;
+  float2 *Hpart, *T, *H2, *xparts;
+  float2 *vb, *vr, *vp, *vy, *vv, *vtmp;
+  float2 *V, *TV;  // lazily allocated (simulation)
+  double* partials;
+  int npartials;
+  unsigned* counter;
+  double* sc;
+  double* hist;
+  int hist_len;
+  int* status;
+  DevMem mem;
+  DevMem lazy;
+  // cached recon graph; captured and replayed on a private stream that is
+  // ordered after / before the caller's stream with events (the legacy
+  // default stream cannot be captured)
+  cudaGraphExec_t gexec;
+  std::vector<char> gkey;
+  cudaStream_t cap_st;
+  cudaEvent_t ev_in, ev_out;
+};
+
+static int auto_nchunk(const gpjc_plan* p) {
+  const int rows = p->ny * p->nz;
+  int n = 1;
+  while ((long long)rows * n < 1024 && n * 2 <= p->nc) n *= 2;
+  return n;
+}
+
+extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil, gpjc_precision prec,
+                                      int32_t nchunk, gpjc_op** out) {
+  if (!gr || !d_coil || !out) return fail(GPJC_EINVAL, "null argument");
+  *out = nullptr;
+  if (prec != GPJC_FP32 && prec != GPJC_BF16) return fail(GPJC_EINVAL, "unknown precision");
+  if (prec == GPJC_BF16) return fail(GPJC_EUNSUPPORTED, "BF16 operator not built in this version");
+  const gpjc_plan* p = gr->plan;
+  if (nchunk < 0 || nchunk > p->nc) return fail(GPJC_EINVAL, "nchunk must be in [0, nc]");
+  auto* op = new (std::nothrow) gpjc_op();
+  if (!op) return fail(GPJC_ENOMEM, "host allocation");
+  std::unique_ptr<gpjc_op> guard(op);
+  op->gr = gr;
+  op->plan = p;
+  op->coil = (const float2*)d_coil;
+  op->prec = prec;
+  op->nchunk = nchunk > 0 ? nchunk : auto_nchunk(p);
+  // workspaces sized for the largest chunk count the autotuner may pick
+  int nmax = op->nchunk;
+  {
+    int n = 1;
+    while (n * 2 <= p->nc && n * 2 <= 16) n *= 2;
+    const size_t per = (size_t)p->ny * p->nz * std::max(p->ntxc, p->nx) * sizeof(float2);
+    while (n > nmax && (size_t)n * per > ((size_t)4 << 30)) n /= 2;
+    nmax = std::max(nmax, n);
+  }
+  op->nchunk_max = nmax;
+  const Geo& g = p->geo;
+  op->L = (size_t)g.rows * g.nx;
+  const size_t HN = (size_t)g.rows * g.ntxc;
+  gpjc_status s;
+  DevMem& m = op->mem;
+  if ((s = m.alloc(&op->Hpart, HN * nmax)) || (s = m.alloc(&op->H2, HN)) ||
+      (s = m.alloc(&op->xparts, op->L * nmax)) || (s = m.alloc(&op->vb, op->L)) ||
+      (s = m.alloc(&op->vr, op->L)) || (s = m.alloc(&op->vp, op->L)) || (s = m.alloc(&op->vy, op->L)) ||
+      (s = m.alloc(&op->vv, op->L)) || (s = m.alloc(&op->vtmp, op->L)))
+    return s;
+  op->T = nullptr;
+  if (g.dim3d && (s = m.alloc(&op->T, HN))) return s;
+  op->npartials = std::max(pe_normal_blocks(g, g.ntxc), sum_parts_blocks(op->L)) + 16;
+  op->hist_len = 1 << 14;
+  if ((s = m.alloc(&op->partials, op->npartials)) || (s = m.alloc(&op->counter, 4)) ||
+      (s = m.alloc(&op->sc, SC_N)) || (s = m.alloc(&op->hist, op->hist_len)) || (s = m.alloc(&op->status, 4)))
+    return s;
+  CK(cudaMemset(op->counter, 0, 4 * sizeof(unsigned)));
+  CK(cudaMemset(op->sc, 0, SC_N * sizeof(double)));
+  CK(cudaMemset(op->status, 0, 4 * sizeof(int)));
+  op->V = op->TV = nullptr;
+  op->gexec = nullptr;
+  op->cap_st = nullptr;
+  op->ev_in = op->ev_out = nullptr;
+  CK(cudaStreamCreateWithFlags(&op->cap_st, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&op->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&op->ev_out, cudaEventDisableTiming));
+  *out = guard.release();
+  return GPJC_OK;
+}
+
+extern "C" void gpjc_op_destroy(gpjc_op* op) {
+  if (!op) return;
+  if (op->gexec) cudaGraphExecDestroy(op->gexec);
+  if (op->cap_st) {
+    cudaStreamSynchronize(op->cap_st);
+    cudaStreamDestroy(op->cap_st);
+  }
+  if (op->ev_in) cudaEventDestroy(op->ev_in);
+  if (op->ev_out) cudaEventDestroy(op->ev_out);
+  delete op;
+}
+
+// --- internal launch sequences (no validation) ---
+static gpjc_status op_fwd(const gpjc_op* op, const float2* x, float2* y, cudaStream_t st) {
+  const Geo& g = op->plan->geo;
+  CK(launch_k1_fwd_fp32(g, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st));
+  CK(launch_pe_fwd(g, op->Hpart, op->nchunk, g.ntxc, op->T, y, st));
+  return GPJC_OK;
+}
+
+static gpjc_status op_adj_parts(const gpjc_op* op, const float2* y, cudaStream_t st) {
+  const Geo& g = op->plan->geo;
+  CK(launch_pe_adj(g, y, g.ntxc, op->T, op->H2, st));
+  CK(launch_k1_adj_fp32(g, op->H2, op->coil, op->gr->AT, op->xparts, op->nchunk, st));
+  return GPJC_OK;
+}
+
+// xparts <- chunks of E_c^H E_c x ; *qq <- ||E_c x||^2 (if qq)
+static gpjc_status op_normal_parts(const gpjc_op* op, const float2* x, double* qq, cudaStream_t st) {
+  const Geo& g = op->plan->geo;
+  CK(launch_k1_fwd_fp32(g, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st));
+  CK(launch_pe_normal(g, op->Hpart, op->nchunk, g.ntxc, op->T, op->H2, op->partials, op->counter, qq, st));
+  CK(launch_k1_adj_fp32(g, op->H2, op->coil, op->gr->AT, op->xparts, op->nchunk, st));
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_apply_E(const gpjc_op* op, const float* d_x, float* d_y, void* stream) {
+  if (!op || !d_x || !d_y) return fail(GPJC_EINVAL, "null argument");
+  return op_fwd(op, (const float2*)d_x, (float2*)d_y, (cudaStream_t)stream);
+}
+
+extern "C" gpjc_status gpjc_apply_EH(const gpjc_op* op, const float* d_y, float* d_x, void* stream) {
+  if (!op || !d_x || !d_y) return fail(GPJC_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  gpjc_status s = op_adj_parts(op, (const float2*)d_y, st);
+  if (s) return s;
+  CK(launch_sum_parts(op->xparts, op->nchunk, op->L, (float2*)d_x, nullptr, nullptr, nullptr, st));
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_apply_normal(const gpjc_op* op, const float* d_x, float* d_out, double* d_qq,
+                                         void* stream) {
+  if (!op || !d_x || !d_out) return fail(GPJC_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  gpjc_status s = op_normal_parts(op, (const float2*)d_x, d_qq, st);
+  if (s) return s;
+  CK(launch_sum_parts(op->xparts, op->nchunk, op->L, (float2*)d_out, nullptr, nullptr, nullptr, st));
+  return GPJC_OK;
+}
+
+static gpjc_status ensure_sim_buffers(gpjc_op* op) {
+  const Geo& g = op->plan->geo;
+  const size_t n = (size_t)g.rows * g.nc * g.ntx;
+  gpjc_status s;
+  if (!op->V && (s = op->lazy.alloc(&op->V, n))) return s;
+  if (g.dim3d && !op->TV && (s = op->lazy.alloc(&op->TV, n))) return s;
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_simulate(const gpjc_op* cop, const float* d_x, float* d_S, void* stream) {
+  if (!cop || !d_x || !d_S) return fail(GPJC_EINVAL, "null argument");
+  gpjc_op* op = const_cast<gpjc_op*>(cop);
+  gpjc_status s = ensure_sim_buffers(op);
+  if (s) return s;
+  const Geo& g = op->plan->geo;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(launch_sim_fwd(g, (const float2*)d_x, op->coil, op->V, op->nchunk, st));
+  CK(launch_pe_fwd(g, op->V, 1, g.nc * g.ntx, op->TV, (float2*)d_S, st));
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_simulate_adjoint(const gpjc_op* cop, const float* d_S, float* d_x, void* stream) {
+  if (!cop || !d_x || !d_S) return fail(GPJC_EINVAL, "null argument");
+  gpjc_op* op = const_cast<gpjc_op*>(cop);
+  gpjc_status s = ensure_sim_buffers(op);
+  if (s) return s;
+  const Geo& g = op->plan->geo;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(launch_pe_adj(g, (const float2*)d_S, g.nc * g.ntx, op->TV, op->V, st));
+  CK(launch_sim_adj(g, op->V, op->coil, op->xparts, op->nchunk, st));
+  CK(launch_sum_parts(op->xparts, op->nchunk, op->L, (float2*)d_x, nullptr, nullptr, nullptr, st));
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchunk_out) {
+  if (!op) return fail(GPJC_EINVAL, "null operator");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int keep = op->nchunk;
+  float best = 1e30f;
+  int best_n = keep;
+  for (int n = 1; n <= op->nchunk_max; n *= 2) {
+    op->nchunk = n;
+    gpjc_status s = op_normal_parts(op, op->vv, nullptr, st);  // warm-up
+    if (s) {
+      op->nchunk = keep;
+      return s;
+    }
+    CK(cudaEventRecord(e0, st));
+    for (int r = 0; r < 5; ++r) op_normal_parts(op, op->vv, nullptr, st);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      best_n = n;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  op->nchunk = best_n;
+  if (op->gexec) {
+    cudaGraphExecDestroy(op->gexec);
+    op->gexec = nullptr;
+    op->gkey.clear();
+  }
+  if (nchunk_out) *nchunk_out = best_n;
+  return GPJC_OK;
+}
+
+// ------------------------------------------------------------------ recon --
+static gpjc_status recon_body(gpjc_op* op, const float2* Sc, float2* x, const gpjc_recon_params& rp,
+                              cudaStream_t st) {
+  const Geo& g = op->plan->geo;
+  const size_t L = op->L;
+  double* sc = op->sc;
+  gpjc_status s;
+  CK(cudaMemsetAsync(op->status, 0, sizeof(int), st));
+  // b = E_c^H S'
+  if ((s = op_adj_parts(op, Sc, st))) return s;
+  CK(launch_sum_parts(op->xparts, op->nchunk, L, op->vb, op->partials, op->counter, sc + SC_BB, st));
+  if (rp.alg == GPJC_CG) {
+    if (rp.use_x0) {
+      if ((s = op_normal_parts(op, x, nullptr, st))) return s;
+      CK(launch_sum_parts(op->xparts, op->nchunk, L, op->vtmp, nullptr, nullptr, nullptr, st));
+      CK(launch_axpby(op->vr, op->vb, op->vtmp, 1.0f, -1.0f, L, st));
+    } else {
+      CK(launch_zero(x, L, st));
+      CK(launch_copy(op->vr, op->vb, L, st));
+    }
+    CK(launch_sum_parts(op->vr, 1, L, op->vp, op->partials, op->counter, sc + SC_RR0, st));
+    CK(cudaMemcpyAsync(op->hist, sc + SC_RR0, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    for (int it = 0; it < rp.iters; ++it) {
+      double* rr = sc + (it % 2 ? SC_RR1 : SC_RR0);
+      double* rrn = sc + (it % 2 ? SC_RR0 : SC_RR1);
+      if ((s = op_normal_parts(op, op->vp, sc + SC_QQ, st))) return s;
+      double* h = (it + 1 < op->hist_len) ? op->hist + it + 1 : nullptr;
+      CK(launch_cg_update1(op->xparts, op->nchunk, L, x, op->vr, op->vp, rr, sc + SC_QQ, op->partials, op->counter,
+                           rrn, h, op->status, st));
+      CK(launch_cg_update2(op->vp, op->vr, L, rr, rrn, st));
+    }
+    return GPJC_OK;
+  }
+  // FISTA
+  if (rp.lipschitz > 0.0) {
+    CK(launch_set_scalar(sc + SC_LIP, rp.lipschitz, st));
+  } else {
+    const int pit = rp.power_iters > 0 ? rp.power_iters : 20;
+    CK(launch_scale_by(op->vv, op->vb, sc + SC_BB, L, nullptr, st));
+    for (int it = 0; it < pit; ++it) {
+      if ((s = op_normal_parts(op, op->vv, nullptr, st))) return s;
+      CK(launch_sum_parts(op->xparts, op->nchunk, L, op->vtmp, op->partials, op->counter, sc + SC_NV, st));
+      CK(launch_scale_by(op->vv, op->vtmp, sc + SC_NV, L, sc + SC_LIP, st));
+    }
+  }
+  if (!rp.use_x0) CK(launch_zero(x, L, st));
+  CK(launch_copy(op->vy, x, L, st));
+  double t = 1.0;
+  for (int it = 0; it < rp.iters; ++it) {
+    if ((s = op_normal_parts(op, op->vy, nullptr, st))) return s;
+    const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
+    const double ck = (t - 1.0) / tn;
+    CK(launch_fista_step(g, op->xparts, op->nchunk, x, op->vy, op->vb, sc + SC_LIP, rp.lambda, rp.haar_levels, ck,
+                         op->status, st));
+    t = tn;
+  }
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_recon(const gpjc_op* cop, const float* d_Sc, float* d_x, const gpjc_recon_params* params,
+                                  gpjc_recon_info* info, void* stream) {
+  if (!cop || !d_Sc || !d_x || !params) return fail(GPJC_EINVAL, "null argument");
+  gpjc_op* op = const_cast<gpjc_op*>(cop);
+  const gpjc_recon_params rp = *params;
+  const Geo& g = op->plan->geo;
+  if (rp.alg != GPJC_CG && rp.alg != GPJC_FISTA) return fail(GPJC_EINVAL, "unknown algorithm");
+  if (rp.iters < 0 || rp.iters > 100000) return fail(GPJC_EINVAL, "iters out of range");
+  if (rp.alg == GPJC_FISTA) {
+    if (rp.haar_levels < 0 || rp.haar_levels > 5) return fail(GPJC_EINVAL, "haar_levels must be in [0, 5]");
+    const int ts = 1 << rp.haar_levels;
+    if (g.nx % ts || g.ny % ts) return fail(GPJC_EINVAL, "nx, ny must be divisible by 2^haar_levels");
+    if (!(rp.lambda >= 0.0) || !std::isfinite(rp.lambda)) return fail(GPJC_EINVAL, "lambda must be finite and >= 0");
+    if (!std::isfinite(rp.lipschitz)) return fail(GPJC_EINVAL, "lipschitz must be finite");
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  gpjc_status s;
+  if (rp.use_graph) {
+    std::vector<char> key(sizeof(rp) + 2 * sizeof(void*) + sizeof(int));
+    memcpy(key.data(), &rp, sizeof(rp));
+    memcpy(key.data() + sizeof(rp), &d_Sc, sizeof(void*));
+    memcpy(key.data() + sizeof(rp) + sizeof(void*), &d_x, sizeof(void*));
+    memcpy(key.data() + sizeof(rp) + 2 * sizeof(void*), &op->nchunk, sizeof(int));
+    cudaStream_t cs = op->cap_st;
+    CK(cudaEventRecord(op->ev_in, st));
+    CK(cudaStreamWaitEvent(cs, op->ev_in, 0));
+    if (!op->gexec || key != op->gkey) {
+      if (op->gexec) {
+        cudaGraphExecDestroy(op->gexec);
+        op->gexec = nullptr;
+        op->gkey.clear();
+      }
+      // one eager pass sets every kernel attribute outside the capture and
+      // produces the result of this call
+      if ((s = recon_body(op, (const float2*)d_Sc, (float2*)d_x, rp, cs))) return s;
+      cudaGraph_t graph;
+      CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+      s = recon_body(op, (const float2*)d_Sc, (float2*)d_x, rp, cs);
+      cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+      if (s) return s;
+      if (ce != cudaSuccess) return fail(GPJC_ECUDA, "stream capture: %s", cudaGetErrorString(ce));
+      ce = cudaGraphInstantiate(&op->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) return fail(GPJC_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
+      op->gkey = key;
+    } else {
+      CK(cudaGraphLaunch(op->gexec, cs));
+    }
+    CK(cudaEventRecord(op->ev_out, cs));
+    CK(cudaStreamWaitEvent(st, op->ev_out, 0));
+  } else {
+    if ((s = recon_body(op, (const float2*)d_Sc, (float2*)d_x, rp, st))) return s;
+  }
+  if (info) {
+    int dev_status = 0;
+    double lip = 0.0;
+    CK(cudaMemcpyAsync(&dev_status, op->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&lip, op->sc + SC_LIP, sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (info->h_history && rp.alg == GPJC_CG) {
+      const int n = std::min(rp.iters + 1, op->hist_len);
+      CK(cudaMemcpyAsync(info->h_history, op->hist, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    info->status = dev_status == kDevNonFinite ? GPJC_ENONFINITE : (dev_status ? GPJC_ETIMEOUT : GPJC_OK);
+    info->lipschitz = lip;
+    if (dev_status) return fail((gpjc_status)info->status, "device status %d", dev_status);
+  }
+  return GPJC_OK;
+}

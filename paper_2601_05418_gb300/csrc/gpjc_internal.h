@@ -1,0 +1,51 @@
+// Internal structures shared by the host API (gpjc_api.cu) and the kernel
+// translation units.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace gpjc {
+
+constexpr int kMaxStages = 12;
+
+// Radix plan of one FFT length (product of 2,3,4,5,7,8).
+struct FftPlan {
+  int n;
+  int nst;
+  int rad[kMaxStages];
+};
+
+// Geometry and device-resident bookkeeping tables, passed to kernels by
+// value.  All pointers are device pointers owned by the plan.
+struct Geo {
+  int nx, ny, nz, nc, os, ntx, w, G, ns, np, ntxc, rows, n_lines, keep_max;
+  int dim3d;  // nz > 1
+  float inv_sqrt_ntx, inv_sqrt_ny, inv_sqrt_nz;
+  FftPlan fx, fy, fz;
+  const int* pg;          // [np] patch -> group
+  const int* poff;        // [np] first compressed column of patch
+  const int* keep;        // [G]
+  const int* aoff;        // [G] offset of group g inside packed A (complex elems)
+  const int* out_tbase;   // [ntxc] first readout sample of the column's patch
+  const int* out_abase;   // [ntxc] aoff[g] + k for the column
+  const int* out_astride; // [ntxc] keep[g] of the column's group
+  const int* line_ky;     // [n_lines]
+  const int* line_kz;     // [n_lines]
+  const int* line_of;     // [nz*ny] line index of (kz, ky) or -1
+  const float* ay;        // [ntx] wave excursion a_y(t) (phase-encode lines)
+  const float* az;        // [ntx]
+  const float2* tw_x;     // [nx] exp(-2 pi i k / nx)
+  const float2* tw_y;     // [ny]
+  const float2* tw_z;     // [nz]
+  const float2* pre;      // [os * nx] (-1)^x exp(-2 pi i s x / ntx)
+};
+
+// Device status word values (written by kernels, read by the host).
+enum DevStatus : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2, kDevBadIndex = 3 };
+
+// Shared-memory budget of one k1 block (readout stage) for a geometry.
+inline size_t k1_smem_bytes(const Geo& g) {
+  return sizeof(float2) * (size_t)(4 * g.ntx + g.nx);
+}
+
+}  // namespace gpjc

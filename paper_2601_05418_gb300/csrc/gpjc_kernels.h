@@ -1,0 +1,82 @@
+// Kernel launchers (host functions defined in the kernel translation units).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "gpjc_internal.h"
+
+namespace gpjc {
+
+// ---- plan tables (k_groups.cu)
+cudaError_t launch_make_tables(Geo& g, float2* tw_x, float2* tw_y, float2* tw_z, float2* pre, float* ay,
+                               float* az, double cycles, double kappa_y, double kappa_z, cudaStream_t st);
+
+// ---- operator (k_operator.cu)
+cudaError_t launch_k1_fwd_fp32(const Geo& g, const float2* x, const float2* coil, const float2* AT,
+                               float2* Hpart, int nchunk, cudaStream_t st);
+cudaError_t launch_k1_adj_fp32(const Geo& g, const float2* H2, const float2* coil, const float2* AT,
+                               float2* xpart, int nchunk, cudaStream_t st);
+cudaError_t launch_sim_fwd(const Geo& g, const float2* x, const float2* coil, float2* V, int nchunk,
+                           cudaStream_t st);
+cudaError_t launch_sim_fwd_bf16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
+                                cudaStream_t st);
+cudaError_t launch_sim_adj(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
+                           cudaStream_t st);
+cudaError_t launch_sim_adj_bf16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,
+                                cudaStream_t st);
+cudaError_t launch_pe_fwd(const Geo& g, const float2* Hpart, int nchunk, int ncols, float2* T, float2* Sc,
+                          cudaStream_t st);
+cudaError_t launch_pe_adj(const Geo& g, const float2* Sc, int ncols, float2* T, float2* H, cudaStream_t st);
+cudaError_t launch_pe_normal(const Geo& g, const float2* Hpart, int nchunk, int ncols, float2* T, float2* H2,
+                             double* partials, unsigned* counter, double* qq, cudaStream_t st);
+int pe_normal_blocks(const Geo& g, int ncols);
+
+// ---- groups (k_groups.cu)
+cudaError_t launch_roi_count(const Geo& g, const float2* coil, const uint8_t* roi, int* blockcount, int nblk,
+                             cudaStream_t st);
+cudaError_t launch_roi_scan(const int* blockcount, int* blockoff, int nblk, int* total, cudaStream_t st);
+cudaError_t launch_roi_compact(const Geo& g, const float2* coil, const uint8_t* roi, const int* blockoff,
+                               int* pix, int nblk, cudaStream_t st);
+cudaError_t launch_roi_coils(const Geo& g, const float2* coil, const float2* T, const int* pix, int K, int Kpad,
+                             float2* chat, cudaStream_t st);
+int roi_block_pixels();
+cudaError_t launch_gram(const Geo& g, const float2* chat, const int* pix, int K, int Kpad, const int* pref,
+                        double2* P, cudaStream_t st);
+cudaError_t launch_hermitize(const Geo& g, double2* P, cudaStream_t st);
+cudaError_t launch_eig_init(const Geo& g, int b, double2* X, cudaStream_t st);
+cudaError_t launch_eig_matmul(const Geo& g, int b, const double2* P, const double2* X, double2* Y,
+                              cudaStream_t st);
+cudaError_t launch_eig_orth(const Geo& g, int b, double2* Y, cudaStream_t st);
+cudaError_t launch_eig_project(const Geo& g, int b, const double2* Q, const double2* Z, double2* Hm,
+                               cudaStream_t st);
+cudaError_t launch_eig_jacobi(const Geo& g, int b, double2* Hm, double2* W, double* ritz, int* order,
+                              int max_sweeps, cudaStream_t st);
+cudaError_t launch_eig_rotate(const Geo& g, int b, const double2* Q, const double2* W, const int* order,
+                              double2* U, cudaStream_t st);
+cudaError_t launch_eig_residual(const Geo& g, int b, const double2* PU, const double2* U, const double* ritz,
+                                const int* order, double* resid, cudaStream_t st);
+cudaError_t launch_form_A(const Geo& g, int b, const double2* U, const float2* T, float2* A, float2* AT,
+                          float* scale, cudaStream_t st);
+cudaError_t launch_compress_fp32(const Geo& g, const float2* S, int n_lines_in, const float2* AT, float2* Sc,
+                                 cudaStream_t st);
+
+// ---- recon (k_recon.cu)
+cudaError_t launch_sum_parts(const float2* parts, int nchunk, size_t L, float2* out, double* partials,
+                             unsigned* counter, double* nrm2, cudaStream_t st);
+int sum_parts_blocks(size_t L);
+cudaError_t launch_cg_update1(const float2* parts, int nchunk, size_t L, float2* x, float2* r, const float2* p,
+                              const double* rr, const double* qq, double* partials, unsigned* counter,
+                              double* rr_new, double* hist, int* status, cudaStream_t st);
+cudaError_t launch_cg_update2(float2* p, const float2* r, size_t L, const double* rr, const double* rr_new,
+                              cudaStream_t st);
+cudaError_t launch_axpby(float2* y, const float2* a, const float2* b, float alpha, float beta, size_t L,
+                         cudaStream_t st);
+cudaError_t launch_scale_by(float2* v, const float2* src, const double* nrm2, size_t L, double* Lout,
+                            cudaStream_t st);
+cudaError_t launch_fista_step(const Geo& g, const float2* parts, int nchunk, float2* x, float2* y,
+                              const float2* b, const double* Lip, double lam, int levels, double ck,
+                              int* status, cudaStream_t st);
+cudaError_t launch_copy(float2* dst, const float2* src, size_t n, cudaStream_t st);
+cudaError_t launch_zero(float2* dst, size_t n, cudaStream_t st);
+cudaError_t launch_set_scalar(double* d, double v, cudaStream_t st);
+
+}  // namespace gpjc

@@ -1,0 +1,90 @@
+"""The C ABI library loads, exports every declared entry point and rejects
+invalid requests on the host before touching a device (CPU only)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "gpjc.h")
+
+
+@pytest.fixture(scope="module")
+def gpjc():
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_05418_gb300 import gpjc as m
+
+    return m
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(gpjc_[A-Za-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_five_hot_path_calls():
+    names = declared_functions()
+    for n in ("gpjc_build_groups", "gpjc_compress", "gpjc_apply_E", "gpjc_apply_EH", "gpjc_recon"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(gpjc):
+    lib = gpjc.lib()
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_version(gpjc):
+    lib = gpjc.lib()
+    for s in range(7):
+        assert lib.gpjc_strerror(s)
+    assert b"sm_103a" in lib.gpjc_version()
+
+
+def _geom(gpjc, **kw):
+    from paper_2601_05418_gb300 import synth
+
+    g = synth.tiny_geometry(nx=8, ny=6, nz=1, nc=2, os=2, cycles=2.0, n_groups=2, keep=3, lines="regular")
+    for k, v in kw.items():
+        setattr(g, k, v)
+    return g
+
+
+@pytest.mark.parametrize("change,needle", [
+    (dict(nx=7), "even"),
+    (dict(ny=0), "even"),
+    (dict(nc=0), "nc"),
+    (dict(w=3), "w must divide"),
+    (dict(nx=22), "products of 2, 3, 5, 7"),
+    (dict(keep=np.array([0, 3], np.int32)), "keep"),
+    (dict(keep=np.array([3, 99], np.int32)), "keep"),
+    (dict(patch_group=np.array([0, 0, 0, 0], np.int32)), "no patch"),
+    (dict(patch_group=np.array([0, 1, 2, 0], np.int32)), "out of range"),
+    (dict(line_ky=np.array([2, 0, 4], np.int32), line_kz=np.zeros(3, np.int32)), "sorted"),
+    (dict(line_ky=np.array([0, 6], np.int32), line_kz=np.zeros(2, np.int32)), "outside"),
+    (dict(cycles=float("nan")), "finite"),
+])
+def test_plan_validation_rejects_before_launch(gpjc, change, needle):
+    g = _geom(gpjc, **change)
+    with pytest.raises(gpjc.GpjcError) as ei:
+        gpjc.Plan(g)
+    assert ei.value.status == gpjc.GPJC_EINVAL
+    assert needle in str(ei.value)
+
+
+def test_null_arguments(gpjc):
+    lib = gpjc.lib()
+    out = C.c_void_p()
+    assert lib.gpjc_plan_create(None, C.byref(out)) == gpjc.GPJC_EINVAL
+    assert lib.gpjc_apply_E(None, None, None, None) == gpjc.GPJC_EINVAL
+    assert lib.gpjc_apply_EH(None, None, None, None) == gpjc.GPJC_EINVAL
+    assert lib.gpjc_compress(None, None, None, 0, None) == gpjc.GPJC_EINVAL
+    assert lib.gpjc_recon(None, None, None, None, None, None) == gpjc.GPJC_EINVAL
+    assert lib.gpjc_build_groups(None, None, None, None, None, None, C.byref(out)) == gpjc.GPJC_EINVAL
+    assert b"null" in lib.gpjc_last_error()
