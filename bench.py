@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Benchmark of the group-patch joint compression hot path on GB300.
+
+One step = the whole hot path for one 2D slice, inputs resident in HBM:
+  groups (ROI compaction, Gram, eigen-decomposition, A_g)  -> compression of
+  the raw k-space (Eq. 13) -> compressed reconstruction (power iteration for
+  the FISTA step + FISTA l1-Haar, or CG-SENSE), all through the C ABI.
+
+Metric: E_c+E_c^H pairs per second over the whole step (every pair of the
+power iteration and the reconstruction counted; the group build and the
+compression add to the time, not to the count), with the per-slice time
+reported beside it.  N > 1 GPUs: one rank per GPU, each on its own slice
+(weak scaling, no collective on the data path).
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the reference arm for this method).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "E_c+E_c^H pairs/s and recon s/slice vs plain FP32 GPU at NRMSE<=1e-3"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpjc", choices=["gpjc", "reference"])
+    ap.add_argument("--workload", default="2d256", choices=["2d256", "2d256bf", "2d128"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(prefix="gpjc_clocks_", suffix=".csv")
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ---------------------------------------------------------------- roofline --
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def k1_flops(g, ntxc, keep_avg):
+    """Algorithmic FP32 flops of one readout-stage launch (all rows, all
+    coils): coil multiply (6 N_x), pre-twiddle (6 N_tx), os FFTs of N_x
+    points (5 N_x log2 N_x each), wave/centring post-multiply (6 N_tx) and the
+    A_g contraction (8 flops per complex MAC, N_s'_g x w per patch and coil)."""
+    rows = g.ny * g.nz
+    per_coil_row = (6 * g.nx + 6 * g.ntx + g.os * 5 * g.nx * math.log2(g.nx) + 6 * g.ntx
+                    + 8 * ntxc * g.w)
+    return rows * g.nc * per_coil_row
+
+
+# ---------------------------------------------------------------- gpjc arm --
+def run_gpjc(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_05418_gb300 import gpjc, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    wl = synth.workload(args.workload)
+    g = wl.geom
+    case = synth.make_case(wl)
+    prec = gpjc.BF16 if wl.precision == "bf16" else gpjc.FP32
+    plan = gpjc.Plan(g)
+    coils_h = torch.from_numpy(case.coils.astype(np.complex64)).pin_memory()
+    roi_h = torch.from_numpy(case.roi).pin_memory()
+    coils = coils_h.to(dev)
+    roi = roi_h.to(dev)
+    rho = torch.from_numpy(case.rho.astype(np.complex64)).to(dev)
+    noise = torch.from_numpy(case.noise.astype(np.complex64)).to(dev)
+    grp = gpjc.Groups.build(plan, coils, roi)
+    op = gpjc.Operator(grp, coils, prec)
+    op.autotune()
+    S = op.simulate(rho) + noise  # raw k-space of this slice, resident in HBM
+    torch.cuda.synchronize()
+    S_h = S.cpu().pin_memory()
+    Sc = torch.empty((g.n_lines, plan.ntx_c), dtype=torch.complex64, device=dev)
+    x = torch.empty(g.shape, dtype=torch.complex64, device=dev)
+    power_iters = 20
+    pairs_per_step = wl.iters + (power_iters if wl.alg == "fista" else 0)
+
+    def step():
+        grp.rebuild(coils, roi)
+        gpjc.compress(grp, S, prec, out=Sc)
+        if wl.alg == "fista":
+            op.recon(Sc, alg=gpjc.FISTA, iters=wl.iters, lam=wl.lam, power_iters=power_iters,
+                     haar_levels=wl.haar_levels, out=x, sync=False)
+        else:
+            op.recon(Sc, alg=gpjc.CG, iters=wl.iters, out=x, sync=False)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+    op.profile(True)  # stage events are part of the captured graph from the first call on
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- timed region (device events per step; L2 flushed between steps)
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = gpjc.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    prof = {s: [0.0, 0] for s in (gpjc.STAGE_READOUT_FWD, gpjc.STAGE_PHASE_ENCODE, gpjc.STAGE_READOUT_ADJ)}
+    barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        for s in prof:
+            ms, n = op.profile_read(s)
+            prof[s][0] += ms
+            prof[s][1] += n
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    launches = gpjc.launch_count() - launches0
+    clocks = sampler.stop()
+    op.profile(False)
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(ms_steps)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = pairs_per_step * args.steps * world / (total_ms / 1e3)
+
+    # ---- dominant kernel and its roofline (FP32 ALU bound)
+    names = {gpjc.STAGE_READOUT_FWD: "k1_fwd_fp32 (readout FFT + PSF + A_g)",
+             gpjc.STAGE_PHASE_ENCODE: "k2 (phase-encode FFT / mask projection)",
+             gpjc.STAGE_READOUT_ADJ: "k1_adj_fp32 (A_g^H + inverse readout FFT + coil sum)"}
+    dom = max(prof, key=lambda s: prof[s][0])
+    dom_ms = prof[dom][0] / max(prof[dom][1], 1)
+    keep_avg = float(np.mean(g.keep))
+    fl = k1_flops(g, plan.ntx_c, keep_avg)
+    sm_mhz = clocks["sm_mhz"] or 2070.0
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled SM clock
+    achieved = fl / (dom_ms * 1e-3) / 1e12
+    roofline = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4), "traffic": None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled SM clock)",
+                "launch_ms": round(dom_ms, 5),
+                "stage_share": {names[s]: round(prof[s][0] / max(total_ms, 1e-9), 4) for s in prof}}
+
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        x_h = torch.empty(g.shape, dtype=torch.complex64).pin_memory()
+        e2e_steps = args.steps
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            coils.copy_(coils_h, non_blocking=True)
+            roi.copy_(roi_h, non_blocking=True)
+            S.copy_(S_h, non_blocking=True)
+            step()
+            x_h.copy_(x, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        e2e_ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        h2d = coils_h.numel() * 8 + roi_h.numel() + S_h.numel() * 8
+        e2e = {"value": round(pairs_per_step * e2e_steps * world / (e2e_ms / 1e3), 2), "unit": "pairs/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(x_h.numel() * 8),
+               "s_per_slice": round(e2e_ms / 1e3 / e2e_steps, 6)}
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec == gpjc.BF16 else "f32",
+        "data": "synthetic (seeded phantom, Gaussian-phase coils, regular R=3 mask, sigma 1e-3 noise)",
+        "config": {"workload": wl.name, "matrix": [g.nz, g.ny, g.nx], "coils": g.nc, "os": g.os,
+                   "groups": g.n_groups, "w": g.w, "keep": int(g.keep[0]), "ntx_c": plan.ntx_c,
+                   "n_lines": g.n_lines, "alg": wl.alg, "iters": wl.iters,
+                   "power_iters": power_iters if wl.alg == "fista" else 0, "pairs_per_step": pairs_per_step,
+                   "slices_per_step_per_gpu": 1, "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{world} (one slice per GPU)"},
+        "recon_s_per_slice": round(ms_per_step / 1e3, 6),
+        "wall_s": round(wall, 3),
+        "clocks": clocks,
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, pairs_per_step, power_iters)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------- oracle arm --
+def _oracle_sample(wl, pairs_per_step, power_iters, n_groups_sample=1, n_iters_sample=1):
+    """Time the FP64 oracle on a bounded sample of one step and extrapolate:
+    Gram + eigen-decomposition of `n_groups_sample` groups, compression of
+    the slice, E_c^H S' and `n_iters_sample` E_c^H E_c applications plus the
+    FISTA proximal step.  Returns (seconds per full step, sample description)."""
+    import numpy as np
+
+    import oracle as O
+    from paper_2601_05418_gb300 import synth
+
+    g = wl.geom
+    case = synth.make_case(wl)
+    S = O.simulate(g, case.coils, case.rho, case.noise)
+    idx = O.roi_pixels(case.roi, case.coils)
+    t0 = time.perf_counter()
+    As = []
+    for gi in range(n_groups_sample):
+        P = O.gram(g, case.coils, idx, gi)
+        A, _ = O.compression_matrix(P, int(g.keep[gi]), g.nc, g.w)
+        As.append(A)
+    t_groups = (time.perf_counter() - t0) / n_groups_sample * g.n_groups
+    As = As + [As[0]] * (g.n_groups - len(As))
+    t0 = time.perf_counter()
+    Sc = O.compress(g, As, S)
+    t_comp = time.perf_counter() - t0
+    pb = O.Problem(g, case.coils, As)
+    t0 = time.perf_counter()
+    b = pb.EcH(Sc)
+    t_b = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    y = b.copy()
+    for _ in range(n_iters_sample):
+        z = y - (pb.normal_c(y) - b) / 1.0
+        if wl.alg == "fista":
+            y = np.stack([O.wavelet_prox(z[k], wl.lam, wl.haar_levels) for k in range(z.shape[0])])
+    t_it = (time.perf_counter() - t0) / n_iters_sample
+    total = t_groups + t_comp + t_b + t_it * pairs_per_step
+    sample = (f"oracle on {n_groups_sample}/{g.n_groups} groups (Gram+eigh) and {n_iters_sample} of "
+              f"{pairs_per_step} normal-operator iterations of one {wl.name} slice, plus compression and "
+              f"E_c^H S'; extrapolated linearly to the full step")
+    return total, sample
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        return max([i.get("num_threads", 1) for i in threadpool_info()] or [1])
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(wl, pairs_per_step, power_iters):
+    t, sample = _oracle_sample(wl, pairs_per_step, power_iters)
+    return {"value": round(pairs_per_step / t, 4), "unit": "pairs/s", "cores": _blas_threads(), "kind": "oracle",
+            "sample": sample + " (numpy FFT single-threaded, BLAS threaded)", "s_per_slice": round(t, 3)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2601_05418_gb300 import synth
+
+    wl = synth.workload(args.workload)
+    power_iters = 20
+    pairs_per_step = wl.iters + (power_iters if wl.alg == "fista" else 0)
+    for _ in range(args.warmup):
+        _oracle_sample(wl, pairs_per_step, power_iters)
+    ts, sample = [], ""
+    for _ in range(args.steps):
+        t, sample = _oracle_sample(wl, pairs_per_step, power_iters)
+        ts.append(t)
+    t = sum(ts) / len(ts)
+    value = pairs_per_step / t
+    out = {"metric": METRIC, "value": round(value, 4), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl.name, "pairs_per_step": pairs_per_step}, "impl": "reference",
+           "cpu_baseline": {"value": round(value, 4), "unit": "pairs/s", "cores": _blas_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_info()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_gpjc(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -119,11 +119,20 @@ typedef struct gpjc_build_params {
  *   d_roi   [nz][ny][nx] uint8 (nonzero = inside), device
  *   h_T     [nc][nc] complex64 noise-decorrelation matrix (row-major), host, or NULL for identity
  *   params  may be NULL for defaults
- * Synchronises `stream` (the ROI size sizes internal buffers).  *out is
- * released with gpjc_groups_destroy and must not outlive `plan`. */
+ * Synchronises `stream` once (to reject an empty ROI).  The groups keep
+ * their scratch (about G N_s^2 complex128 plus N_C x |grid| complex64) for
+ * gpjc_groups_rebuild.  *out is released with gpjc_groups_destroy and must
+ * not outlive `plan`. */
 gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_coil, const uint8_t* d_roi,
                               const float* h_T, const gpjc_build_params* params, void* stream,
                               gpjc_groups** out);
+
+/* Recomputes the groups of a gpjc_build_groups result from new coil maps
+ * and ROI of the same geometry, reusing its scratch: asynchronous on
+ * `stream`, allocates nothing, synchronises nothing (usable in stream
+ * capture).  An empty ROI yields non-finite A (check with gpjc_groups_info_get). */
+gpjc_status gpjc_groups_rebuild(gpjc_groups* groups, const float* d_coil, const uint8_t* d_roi, const float* h_T,
+                                void* stream);
 
 /* Groups from given matrices (e.g. a stored result, or an external
  * solver): h_A holds A_g row-major [keep_g][N_s] complex64 for g = 0..G-1,
@@ -136,6 +145,7 @@ typedef struct gpjc_groups_info {
   int32_t block;       /* Ritz values per group (b)                     */
   double max_residual; /* max_g max_{k<keep} ||P u - lambda u|| / lambda_0 */
 } gpjc_groups_info;
+/* Synchronous (reads the device results of the last build). */
 gpjc_status gpjc_groups_info_get(const gpjc_groups* groups, gpjc_groups_info* info);
 /* h_A: as gpjc_groups_from_matrices.  h_ritz: [n_groups][block] Ritz values,
  * descending (NULL allowed).  Synchronous. */
@@ -202,6 +212,25 @@ typedef struct gpjc_recon_info {
  * `info` is non-NULL (to report status, L and history). */
 gpjc_status gpjc_recon(const gpjc_op* op, const float* d_Sc, float* d_x, const gpjc_recon_params* params,
                        gpjc_recon_info* info, void* stream);
+
+/* ------------------------------------------------------------------ profiling -- */
+/* Kernels launched by this library in this process (graph replays add the
+ * kernel nodes of the replayed graph).  Thread-safe. */
+uint64_t gpjc_launch_count(void);
+
+typedef enum gpjc_stage {
+  GPJC_STAGE_READOUT_FWD = 0,  /* coil multiply + readout FFT + wave PSF + A_g (E_c, first half) */
+  GPJC_STAGE_PHASE_ENCODE = 1, /* phase-encode FFTs, line gather / scatter / mask projection     */
+  GPJC_STAGE_READOUT_ADJ = 2   /* A_g^H + inverse readout FFT + conj(coil) sum (E_c^H, second half) */
+} gpjc_stage;
+
+/* Enables (1) or disables (0) CUDA-event timing of each operator stage on the
+ * stream the stage runs on; enabling clears earlier marks.  Reconstruction
+ * calls restart the marks.  Not thread-safe with concurrent use of `op`. */
+gpjc_status gpjc_op_profile(gpjc_op* op, int32_t enable);
+/* Sum of the device durations of the marked launches of `stage` since the
+ * last reset, and their number.  Waits for the marked events. */
+gpjc_status gpjc_op_profile_read(const gpjc_op* op, int32_t stage, double* total_ms, int32_t* count);
 
 #ifdef __cplusplus
 }

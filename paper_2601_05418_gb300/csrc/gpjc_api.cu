@@ -19,6 +19,17 @@
 
 using namespace gpjc;
 
+// ------------------------------------------------------------------ launches --
+#include <atomic>
+static std::atomic<unsigned long long> g_launches{0};
+static thread_local bool g_capturing = false;
+namespace gpjc {
+void note_launches(int n) {
+  if (!g_capturing) g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+}
+}  // namespace gpjc
+extern "C" uint64_t gpjc_launch_count(void) { return g_launches.load(); }
+
 // ------------------------------------------------------------------ errors --
 static thread_local std::string g_err;
 
@@ -232,15 +243,17 @@ extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
       (s = m.upload(&d_ky, p->line_ky)) || (s = m.upload(&d_kz, p->line_kz)) ||
       (s = m.upload(&d_lof, p->line_of)))
     return s;
-  float2 *tw_x, *tw_y, *tw_z, *pre;
+  float2 *tw_x, *tw_y, *tw_z, *pre, *post_y, *post_z;
   float *ay, *az;
   if ((s = m.alloc(&tw_x, nx)) || (s = m.alloc(&tw_y, ny)) || (s = m.alloc(&tw_z, nz)) ||
-      (s = m.alloc(&pre, (size_t)ntx)) || (s = m.alloc(&ay, (size_t)ntx)) || (s = m.alloc(&az, (size_t)ntx)))
+      (s = m.alloc(&pre, (size_t)ntx)) || (s = m.alloc(&ay, (size_t)ntx)) || (s = m.alloc(&az, (size_t)ntx)) ||
+      (s = m.alloc(&post_y, (size_t)ny * ntx)) || (s = m.alloc(&post_z, (size_t)nz * ntx)))
     return s;
   g.pg = d_pg; g.poff = d_poff; g.keep = d_keep; g.aoff = d_aoff; g.out_tbase = d_tb; g.out_abase = d_ab;
   g.out_astride = d_as; g.line_ky = d_ky; g.line_kz = d_kz; g.line_of = d_lof; g.ay = ay; g.az = az;
-  g.tw_x = tw_x; g.tw_y = tw_y; g.tw_z = tw_z; g.pre = pre;
+  g.tw_x = tw_x; g.tw_y = tw_y; g.tw_z = tw_z; g.pre = pre; g.post_y = post_y; g.post_z = post_z;
   CK(launch_make_tables(g, tw_x, tw_y, tw_z, pre, ay, az, p->cycles, p->kappa_y, p->kappa_z, 0));
+  CK(launch_make_post(g, post_y, post_z, p->cycles, p->kappa_y, p->kappa_z, 0));
   CK(cudaDeviceSynchronize());
   *out = guard.release();
   return GPJC_OK;
@@ -268,12 +281,24 @@ struct gpjc_groups {
   float2* A;        // [aoff[g] + k ns + i]
   float2* AT;       // [aoff[g] + i keep_g + k]
   float* scale;     // [G]
-  int* pix;         // [K]
-  double2* P;       // optional [G][ns][ns]
-  long long K;
-  int b;
-  std::vector<double> ritz;  // [G][b]
-  double max_resid;
+  int* pix;         // [L] (first K used)
+  int* dK;          // device |ROI|
+  double2* P;       // [G][ns][ns]
+  bool built;       // from coil maps (vs. from matrices)
+  bool keep_gram;
+  int b, iters, nblk, Kpad;
+  // scratch kept for rebuilds, so a rebuild allocates nothing and does
+  // not synchronise
+  int *blockcount, *blockoff, *d_ref;
+  float2 *chat, *dT;
+  double2 *X, *Y, *U, *Hm, *W;
+  double *ritz, *resid;
+  int* order;
+  // host copies, read lazily
+  mutable bool host_valid;
+  mutable long long K;
+  mutable std::vector<double> ritz_h;
+  mutable double max_resid;
   DevMem mem;
 };
 
@@ -286,6 +311,61 @@ static gpjc_status groups_alloc_A(gpjc_groups* gr) {
   return GPJC_OK;
 }
 
+// Asynchronous group build on `st` into the scratch of `gr`.
+static gpjc_status groups_compute(gpjc_groups* gr, const float2* coil, const uint8_t* roi, const float* h_T,
+                                  cudaStream_t st) {
+  const gpjc_plan* plan = gr->plan;
+  const Geo& g = plan->geo;
+  const int b = gr->b;
+  if (h_T) CK(cudaMemcpyAsync(gr->dT, h_T, sizeof(float2) * g.nc * g.nc, cudaMemcpyHostToDevice, st));
+  CK(launch_roi_count(g, coil, roi, gr->blockcount, gr->nblk, st));
+  CK(launch_roi_scan(gr->blockcount, gr->blockoff, gr->nblk, gr->dK, st));
+  CK(launch_roi_compact(g, coil, roi, gr->blockoff, gr->pix, gr->nblk, st));
+  CK(launch_roi_coils(g, coil, h_T ? gr->dT : nullptr, gr->pix, gr->dK, gr->Kpad, gr->chat, st));
+  CK(cudaMemsetAsync(gr->P, 0, sizeof(double2) * (size_t)g.G * g.ns * g.ns, st));
+  CK(launch_gram(g, gr->chat, gr->pix, gr->dK, gr->Kpad, gr->d_ref, gr->P, st));
+  CK(launch_hermitize(g, gr->P, st));
+  double2 *X = gr->X, *Y = gr->Y;
+  CK(launch_eig_init(g, b, X, st));
+  for (int it = 0; it < gr->iters; ++it) {
+    CK(launch_eig_matmul(g, b, gr->P, X, Y, st));
+    CK(launch_eig_orth(g, b, Y, st));
+    std::swap(X, Y);
+  }
+  CK(launch_eig_matmul(g, b, gr->P, X, Y, st));           // Z = P Q
+  CK(launch_eig_project(g, b, X, Y, gr->Hm, st));         // Q^H P Q
+  CK(launch_eig_jacobi(g, b, gr->Hm, gr->W, gr->ritz, gr->order, 60, st));
+  CK(launch_eig_rotate(g, b, X, gr->W, gr->order, gr->U, st));  // Ritz vectors, descending
+  CK(launch_eig_matmul(g, b, gr->P, gr->U, Y, st));       // P U
+  CK(launch_eig_residual(g, b, Y, gr->U, gr->ritz, gr->order, gr->resid, st));
+  CK(launch_form_A(g, b, gr->U, h_T ? gr->dT : nullptr, gr->A, gr->AT, gr->scale, st));
+  gr->host_valid = false;
+  return GPJC_OK;
+}
+
+// Reads |ROI|, Ritz values and residuals back (synchronous).
+static gpjc_status groups_sync_host(const gpjc_groups* gr) {
+  if (gr->host_valid || !gr->built) return GPJC_OK;
+  const Geo& g = gr->plan->geo;
+  const int b = gr->b;
+  int K = 0;
+  std::vector<double> rz((size_t)g.G * b), rs(g.G);
+  std::vector<int> ord((size_t)g.G * b);
+  CK(cudaDeviceSynchronize());
+  CK(cudaMemcpy(&K, gr->dK, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(rz.data(), gr->ritz, sizeof(double) * rz.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ord.data(), gr->order, sizeof(int) * ord.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(rs.data(), gr->resid, sizeof(double) * rs.size(), cudaMemcpyDeviceToHost));
+  gr->K = K;
+  gr->ritz_h.resize(rz.size());
+  for (int gg = 0; gg < g.G; ++gg)
+    for (int r = 0; r < b; ++r) gr->ritz_h[(size_t)gg * b + r] = rz[(size_t)gg * b + ord[(size_t)gg * b + r]];
+  gr->max_resid = 0.0;
+  for (double v : rs) gr->max_resid = std::max(gr->max_resid, v);
+  gr->host_valid = true;
+  return GPJC_OK;
+}
+
 extern "C" gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_coil, const uint8_t* d_roi,
                                          const float* h_T, const gpjc_build_params* params, void* stream,
                                          gpjc_groups** out) {
@@ -295,7 +375,7 @@ extern "C" gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_c
   const Geo& g = plan->geo;
   gpjc_build_params bp = {0, 0, 0};
   if (params) bp = *params;
-  const int iters = bp.eig_iters > 0 ? bp.eig_iters : 12;
+  if (bp.eig_iters < 0 || bp.eig_iters > 1000) return fail(GPJC_EINVAL, "eig_iters out of range");
   int b = bp.block;
   if (b <= 0) b = std::min(plan->ns, std::min(96, std::max(2 * plan->keep_max, plan->keep_max + 16)));
   if (b < plan->keep_max || b > plan->ns) return fail(GPJC_EINVAL, "block %d must be in [keep_max, N_s]", b);
@@ -305,85 +385,40 @@ extern "C" gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_c
   std::unique_ptr<gpjc_groups> guard(gr);
   gr->plan = plan;
   gr->b = b;
+  gr->iters = bp.eig_iters > 0 ? bp.eig_iters : 12;
+  gr->keep_gram = bp.keep_gram != 0;
+  gr->built = true;
+  gr->host_valid = false;
   gpjc_status s;
   if ((s = groups_alloc_A(gr))) return s;
-  DevMem tmp;
+  DevMem& m = gr->mem;
   const size_t L = (size_t)g.rows * g.nx;
-  const int bp_pix = roi_block_pixels();
-  const int nblk = (int)((L + bp_pix - 1) / bp_pix);
-  int *blockcount, *blockoff, *total, *pix;
-  if ((s = tmp.alloc(&blockcount, nblk)) || (s = tmp.alloc(&blockoff, nblk)) || (s = tmp.alloc(&total, 1)) ||
-      (s = gr->mem.alloc(&pix, L)))
-    return s;
-  gr->pix = pix;
-  const float2* coil = (const float2*)d_coil;
-  CK(launch_roi_count(g, coil, d_roi, blockcount, nblk, st));
-  CK(launch_roi_scan(blockcount, blockoff, nblk, total, st));
-  CK(launch_roi_compact(g, coil, d_roi, blockoff, pix, nblk, st));
-  int K = 0;
-  CK(cudaMemcpyAsync(&K, total, sizeof(int), cudaMemcpyDeviceToHost, st));
-  CK(cudaStreamSynchronize(st));
-  if (K <= 0) return fail(GPJC_EINVAL, "ROI is empty (or no coil sees it)");
-  gr->K = K;
-  const int Kpad = ((K + 31) / 32) * 32;
-  float2 *chat, *dT = nullptr;
-  if ((s = tmp.alloc(&chat, (size_t)g.nc * Kpad))) return s;
-  if (h_T) {
-    if ((s = tmp.alloc(&dT, (size_t)g.nc * g.nc))) return s;
-    CK(cudaMemcpyAsync(dT, h_T, sizeof(float2) * g.nc * g.nc, cudaMemcpyHostToDevice, st));
-  }
-  CK(launch_roi_coils(g, coil, dT, pix, K, Kpad, chat, st));
-  // Gram
-  double2* P;
-  DevMem& pm = bp.keep_gram ? gr->mem : tmp;
-  if ((s = pm.alloc(&P, (size_t)g.G * g.ns * g.ns))) return s;
-  CK(cudaMemsetAsync(P, 0, sizeof(double2) * (size_t)g.G * g.ns * g.ns, st));
-  int* d_ref;
-  {
-    std::vector<int> ref(plan->ref.begin(), plan->ref.end());
-    if ((s = tmp.alloc(&d_ref, ref.size()))) return s;
-    CK(cudaMemcpyAsync(d_ref, ref.data(), sizeof(int) * ref.size(), cudaMemcpyHostToDevice, st));
-    CK(launch_gram(g, chat, pix, K, Kpad, d_ref, P, st));
-    CK(launch_hermitize(g, P, st));
-    CK(cudaStreamSynchronize(st));  // ref vector leaves scope
-  }
-  if (bp.keep_gram) gr->P = P;
-  // subspace iteration
+  gr->nblk = (int)((L + roi_block_pixels() - 1) / roi_block_pixels());
+  gr->Kpad = (int)(((L + 31) / 32) * 32);
   const size_t nb = (size_t)g.G * g.ns * b;
-  double2 *X, *Y, *Hm, *W, *U;
-  double *ritz, *resid;
-  int* order;
-  if ((s = tmp.alloc(&X, nb)) || (s = tmp.alloc(&Y, nb)) || (s = tmp.alloc(&U, nb)) ||
-      (s = tmp.alloc(&Hm, (size_t)g.G * b * b)) || (s = tmp.alloc(&W, (size_t)g.G * b * b)) ||
-      (s = tmp.alloc(&ritz, (size_t)g.G * b)) || (s = tmp.alloc(&order, (size_t)g.G * b)) ||
-      (s = tmp.alloc(&resid, (size_t)g.G)))
+  if ((s = m.alloc(&gr->blockcount, gr->nblk)) || (s = m.alloc(&gr->blockoff, gr->nblk)) ||
+      (s = m.alloc(&gr->dK, 1)) || (s = m.alloc(&gr->pix, L)) || (s = m.alloc(&gr->chat, (size_t)g.nc * gr->Kpad)) ||
+      (s = m.alloc(&gr->dT, (size_t)g.nc * g.nc)) || (s = m.alloc(&gr->d_ref, g.G)) ||
+      (s = m.alloc(&gr->P, (size_t)g.G * g.ns * g.ns)) || (s = m.alloc(&gr->X, nb)) || (s = m.alloc(&gr->Y, nb)) ||
+      (s = m.alloc(&gr->U, nb)) || (s = m.alloc(&gr->Hm, (size_t)g.G * b * b)) ||
+      (s = m.alloc(&gr->W, (size_t)g.G * b * b)) || (s = m.alloc(&gr->ritz, (size_t)g.G * b)) ||
+      (s = m.alloc(&gr->order, (size_t)g.G * b)) || (s = m.alloc(&gr->resid, (size_t)g.G)))
     return s;
-  CK(launch_eig_init(g, b, X, st));
-  for (int it = 0; it < iters; ++it) {
-    CK(launch_eig_matmul(g, b, P, X, Y, st));
-    CK(launch_eig_orth(g, b, Y, st));
-    std::swap(X, Y);
-  }
-  CK(launch_eig_matmul(g, b, P, X, Y, st));        // Z = P Q
-  CK(launch_eig_project(g, b, X, Y, Hm, st));      // Q^H P Q
-  CK(launch_eig_jacobi(g, b, Hm, W, ritz, order, 60, st));
-  CK(launch_eig_rotate(g, b, X, W, order, U, st)); // Ritz vectors, descending
-  CK(launch_eig_matmul(g, b, P, U, Y, st));        // P U
-  CK(launch_eig_residual(g, b, Y, U, ritz, order, resid, st));
-  CK(launch_form_A(g, b, U, dT, gr->A, gr->AT, gr->scale, st));
-  std::vector<double> rz((size_t)g.G * b), rs(g.G);
-  std::vector<int> ord((size_t)g.G * b);
-  CK(cudaMemcpyAsync(rz.data(), ritz, sizeof(double) * rz.size(), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(ord.data(), order, sizeof(int) * ord.size(), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(rs.data(), resid, sizeof(double) * rs.size(), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpy(gr->d_ref, plan->ref.data(), sizeof(int) * g.G, cudaMemcpyHostToDevice));
+  if ((s = groups_compute(gr, (const float2*)d_coil, d_roi, h_T, st))) return s;
+  // the ROI must not be empty: checked once here (later rebuilds are asynchronous)
   CK(cudaStreamSynchronize(st));
-  gr->ritz.resize(rz.size());
-  for (int gg = 0; gg < g.G; ++gg)
-    for (int r = 0; r < b; ++r) gr->ritz[(size_t)gg * b + r] = rz[(size_t)gg * b + ord[(size_t)gg * b + r]];
-  gr->max_resid = 0.0;
-  for (double v : rs) gr->max_resid = std::max(gr->max_resid, v);
+  if ((s = groups_sync_host(gr))) return s;
+  if (gr->K <= 0) return fail(GPJC_EINVAL, "ROI is empty (or no coil sees it)");
   *out = guard.release();
   return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_groups_rebuild(gpjc_groups* gr, const float* d_coil, const uint8_t* d_roi,
+                                           const float* h_T, void* stream) {
+  if (!gr || !d_coil || !d_roi) return fail(GPJC_EINVAL, "null argument");
+  if (!gr->built) return fail(GPJC_EINVAL, "groups were created from matrices");
+  return groups_compute(gr, (const float2*)d_coil, d_roi, h_T, (cudaStream_t)stream);
 }
 
 extern "C" gpjc_status gpjc_groups_from_matrices(const gpjc_plan* plan, const float* h_A, gpjc_groups** out) {
@@ -396,6 +431,10 @@ extern "C" gpjc_status gpjc_groups_from_matrices(const gpjc_plan* plan, const fl
   gr->b = 0;
   gr->K = 0;
   gr->max_resid = 0.0;
+  gr->built = false;
+  gr->host_valid = true;
+  gr->P = nullptr;
+  gr->pix = nullptr;
   gpjc_status s;
   if ((s = groups_alloc_A(gr))) return s;
   const size_t na = (size_t)plan->aoff.back() + (size_t)plan->ns * plan->keep.back();
@@ -423,6 +462,8 @@ extern "C" void gpjc_groups_destroy(gpjc_groups* groups) { delete groups; }
 
 extern "C" gpjc_status gpjc_groups_info_get(const gpjc_groups* gr, gpjc_groups_info* info) {
   if (!gr || !info) return fail(GPJC_EINVAL, "null argument");
+  gpjc_status s = groups_sync_host(gr);
+  if (s) return s;
   info->roi_pixels = gr->K;
   info->block = gr->b;
   info->max_residual = gr->max_resid;
@@ -433,14 +474,16 @@ extern "C" gpjc_status gpjc_groups_get(const gpjc_groups* gr, float* h_A, double
   if (!gr) return fail(GPJC_EINVAL, "null groups");
   const gpjc_plan* p = gr->plan;
   const size_t na = (size_t)p->aoff.back() + (size_t)p->ns * p->keep.back();
+  gpjc_status s = groups_sync_host(gr);
+  if (s) return s;
   if (h_A) CK(cudaMemcpy(h_A, gr->A, sizeof(float2) * na, cudaMemcpyDeviceToHost));
-  if (h_ritz && !gr->ritz.empty()) std::copy(gr->ritz.begin(), gr->ritz.end(), h_ritz);
+  if (h_ritz && !gr->ritz_h.empty()) std::copy(gr->ritz_h.begin(), gr->ritz_h.end(), h_ritz);
   return GPJC_OK;
 }
 
 extern "C" gpjc_status gpjc_groups_gram(const gpjc_groups* gr, double* h_P) {
   if (!gr || !h_P) return fail(GPJC_EINVAL, "null argument");
-  if (!gr->P) return fail(GPJC_EINVAL, "groups were built without keep_gram");
+  if (!gr->P || !gr->keep_gram) return fail(GPJC_EINVAL, "groups were built without keep_gram");
   const gpjc_plan* p = gr->plan;
   CK(cudaMemcpy(h_P, gr->P, sizeof(double2) * (size_t)p->G * p->ns * p->ns, cudaMemcpyDeviceToHost));
   return GPJC_OK;
@@ -448,6 +491,8 @@ extern "C" gpjc_status gpjc_groups_gram(const gpjc_groups* gr, double* h_P) {
 
 extern "C" gpjc_status gpjc_groups_roi(const gpjc_groups* gr, int32_t* h_pix) {
   if (!gr || !h_pix) return fail(GPJC_EINVAL, "null argument");
+  gpjc_status s = groups_sync_host(gr);
+  if (s) return s;
   if (gr->K <= 0) return fail(GPJC_EINVAL, "groups were not built from a ROI");
   CK(cudaMemcpy(h_pix, gr->pix, sizeof(int) * (size_t)gr->K, cudaMemcpyDeviceToHost));
   return GPJC_OK;
@@ -490,9 +535,28 @@ struct gpjc_op {
   // default stream cannot be captured)
   cudaGraphExec_t gexec;
   std::vector<char> gkey;
+  int graph_kernels;
   cudaStream_t cap_st;
   cudaEvent_t ev_in, ev_out;
+  // optional per-stage timing with events (GPJC_STAGE_*)
+  bool prof_on;
+  std::vector<cudaEvent_t> prof_pool;
+  size_t prof_used;
+  std::vector<std::pair<int, size_t>> prof_marks;  // (stage, index of start event)
 };
+
+// records the start / end of a stage when profiling is on
+static void prof_begin(gpjc_op* op, int stage, cudaStream_t st, size_t* mark) {
+  *mark = (size_t)-1;
+  if (!op->prof_on || op->prof_used + 2 > op->prof_pool.size()) return;
+  *mark = op->prof_used;
+  op->prof_used += 2;
+  op->prof_marks.push_back({stage, *mark});
+  cudaEventRecord(op->prof_pool[*mark], st);
+}
+static void prof_end(gpjc_op* op, cudaStream_t st, size_t mark) {
+  if (mark != (size_t)-1) cudaEventRecord(op->prof_pool[mark + 1], st);
+}
 
 static int auto_nchunk(const gpjc_plan* p) {
   const int rows = p->ny * p->nz;
@@ -549,6 +613,9 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   CK(cudaMemset(op->status, 0, 4 * sizeof(int)));
   op->V = op->TV = nullptr;
   op->gexec = nullptr;
+  op->graph_kernels = 0;
+  op->prof_on = false;
+  op->prof_used = 0;
   op->cap_st = nullptr;
   op->ev_in = op->ev_out = nullptr;
   CK(cudaStreamCreateWithFlags(&op->cap_st, cudaStreamNonBlocking));
@@ -567,30 +634,51 @@ extern "C" void gpjc_op_destroy(gpjc_op* op) {
   }
   if (op->ev_in) cudaEventDestroy(op->ev_in);
   if (op->ev_out) cudaEventDestroy(op->ev_out);
+  for (cudaEvent_t e : op->prof_pool) cudaEventDestroy(e);
   delete op;
 }
 
 // --- internal launch sequences (no validation) ---
-static gpjc_status op_fwd(const gpjc_op* op, const float2* x, float2* y, cudaStream_t st) {
+static gpjc_status op_fwd(const gpjc_op* cop, const float2* x, float2* y, cudaStream_t st) {
+  gpjc_op* op = const_cast<gpjc_op*>(cop);
   const Geo& g = op->plan->geo;
+  size_t m;
+  prof_begin(op, GPJC_STAGE_READOUT_FWD, st, &m);
   CK(launch_k1_fwd_fp32(g, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st));
+  prof_end(op, st, m);
+  prof_begin(op, GPJC_STAGE_PHASE_ENCODE, st, &m);
   CK(launch_pe_fwd(g, op->Hpart, op->nchunk, g.ntxc, op->T, y, st));
+  prof_end(op, st, m);
   return GPJC_OK;
 }
 
-static gpjc_status op_adj_parts(const gpjc_op* op, const float2* y, cudaStream_t st) {
+static gpjc_status op_adj_parts(const gpjc_op* cop, const float2* y, cudaStream_t st) {
+  gpjc_op* op = const_cast<gpjc_op*>(cop);
   const Geo& g = op->plan->geo;
+  size_t m;
+  prof_begin(op, GPJC_STAGE_PHASE_ENCODE, st, &m);
   CK(launch_pe_adj(g, y, g.ntxc, op->T, op->H2, st));
-  CK(launch_k1_adj_fp32(g, op->H2, op->coil, op->gr->AT, op->xparts, op->nchunk, st));
+  prof_end(op, st, m);
+  prof_begin(op, GPJC_STAGE_READOUT_ADJ, st, &m);
+  CK(launch_k1_adj_fp32(g, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st));
+  prof_end(op, st, m);
   return GPJC_OK;
 }
 
 // xparts <- chunks of E_c^H E_c x ; *qq <- ||E_c x||^2 (if qq)
-static gpjc_status op_normal_parts(const gpjc_op* op, const float2* x, double* qq, cudaStream_t st) {
+static gpjc_status op_normal_parts(const gpjc_op* cop, const float2* x, double* qq, cudaStream_t st) {
+  gpjc_op* op = const_cast<gpjc_op*>(cop);
   const Geo& g = op->plan->geo;
+  size_t m;
+  prof_begin(op, GPJC_STAGE_READOUT_FWD, st, &m);
   CK(launch_k1_fwd_fp32(g, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st));
+  prof_end(op, st, m);
+  prof_begin(op, GPJC_STAGE_PHASE_ENCODE, st, &m);
   CK(launch_pe_normal(g, op->Hpart, op->nchunk, g.ntxc, op->T, op->H2, op->partials, op->counter, qq, st));
-  CK(launch_k1_adj_fp32(g, op->H2, op->coil, op->gr->AT, op->xparts, op->nchunk, st));
+  prof_end(op, st, m);
+  prof_begin(op, GPJC_STAGE_READOUT_ADJ, st, &m);
+  CK(launch_k1_adj_fp32(g, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st));
+  prof_end(op, st, m);
   return GPJC_OK;
 }
 
@@ -698,6 +786,8 @@ static gpjc_status recon_body(gpjc_op* op, const float2* Sc, float2* x, const gp
   const size_t L = op->L;
   double* sc = op->sc;
   gpjc_status s;
+  op->prof_used = 0;
+  op->prof_marks.clear();
   CK(cudaMemsetAsync(op->status, 0, sizeof(int), st));
   // b = E_c^H S'
   if ((s = op_adj_parts(op, Sc, st))) return s;
@@ -787,16 +877,31 @@ extern "C" gpjc_status gpjc_recon(const gpjc_op* cop, const float* d_Sc, float* 
       if ((s = recon_body(op, (const float2*)d_Sc, (float2*)d_x, rp, cs))) return s;
       cudaGraph_t graph;
       CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+      g_capturing = true;
       s = recon_body(op, (const float2*)d_Sc, (float2*)d_x, rp, cs);
+      g_capturing = false;
       cudaError_t ce = cudaStreamEndCapture(cs, &graph);
       if (s) return s;
       if (ce != cudaSuccess) return fail(GPJC_ECUDA, "stream capture: %s", cudaGetErrorString(ce));
+      {
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+        int kn = 0;
+        for (auto nd : nodes) {
+          cudaGraphNodeType ty;
+          if (cudaGraphNodeGetType(nd, &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel) ++kn;
+        }
+        op->graph_kernels = kn;
+      }
       ce = cudaGraphInstantiate(&op->gexec, graph, 0);
       cudaGraphDestroy(graph);
       if (ce != cudaSuccess) return fail(GPJC_ECUDA, "graph instantiate: %s", cudaGetErrorString(ce));
       op->gkey = key;
     } else {
       CK(cudaGraphLaunch(op->gexec, cs));
+      note_launches(op->graph_kernels);
     }
     CK(cudaEventRecord(op->ev_out, cs));
     CK(cudaStreamWaitEvent(st, op->ev_out, 0));
@@ -817,5 +922,40 @@ extern "C" gpjc_status gpjc_recon(const gpjc_op* cop, const float* d_Sc, float* 
     info->lipschitz = lip;
     if (dev_status) return fail((gpjc_status)info->status, "device status %d", dev_status);
   }
+  return GPJC_OK;
+}
+
+// ------------------------------------------------------------------ profiling --
+extern "C" gpjc_status gpjc_op_profile(gpjc_op* op, int32_t enable) {
+  if (!op) return fail(GPJC_EINVAL, "null operator");
+  if (enable && op->prof_pool.empty()) {
+    op->prof_pool.resize(8192);
+    for (auto& e : op->prof_pool) CK(cudaEventCreate(&e));
+  }
+  op->prof_on = enable != 0;
+  op->prof_used = 0;
+  op->prof_marks.clear();
+  if (op->gexec) {  // the cached graph was captured with the other setting
+    cudaGraphExecDestroy(op->gexec);
+    op->gexec = nullptr;
+    op->gkey.clear();
+  }
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_op_profile_read(const gpjc_op* op, int32_t stage, double* total_ms, int32_t* count) {
+  if (!op || !total_ms || !count) return fail(GPJC_EINVAL, "null argument");
+  double tot = 0.0;
+  int n = 0;
+  for (const auto& mk : op->prof_marks) {
+    if (mk.first != stage) continue;
+    CK(cudaEventSynchronize(op->prof_pool[mk.second + 1]));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, op->prof_pool[mk.second], op->prof_pool[mk.second + 1]));
+    tot += ms;
+    ++n;
+  }
+  *total_ms = tot;
+  *count = n;
   return GPJC_OK;
 }

@@ -38,10 +38,16 @@ struct Geo {
   const float2* tw_y;     // [ny]
   const float2* tw_z;     // [nz]
   const float2* pre;      // [os * nx] (-1)^x exp(-2 pi i s x / ntx)
+  const float2* post_y;   // [ny][ntx] (-1)^{m+nx/2} e^{i pi s/os} e^{-2 pi i a_y(t) y_c/ny} / sqrt(ntx)
+  const float2* post_z;   // [nz][ntx] e^{-2 pi i a_z(t) z_c/nz}
 };
 
 // Device status word values (written by kernels, read by the host).
 enum DevStatus : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2, kDevBadIndex = 3 };
+
+// Count of kernels launched by this library (for launch accounting); the
+// launchers add to it unless the calling thread is capturing a graph.
+void note_launches(int n);
 
 // Shared-memory budget of one k1 block (readout stage) for a geometry.
 inline size_t k1_smem_bytes(const Geo& g) {

@@ -9,11 +9,13 @@ namespace gpjc {
 // ---- plan tables (k_groups.cu)
 cudaError_t launch_make_tables(Geo& g, float2* tw_x, float2* tw_y, float2* tw_z, float2* pre, float* ay,
                                float* az, double cycles, double kappa_y, double kappa_z, cudaStream_t st);
+cudaError_t launch_make_post(const Geo& g, float2* post_y, float2* post_z, double cycles, double kappa_y,
+                             double kappa_z, cudaStream_t st);
 
 // ---- operator (k_operator.cu)
 cudaError_t launch_k1_fwd_fp32(const Geo& g, const float2* x, const float2* coil, const float2* AT,
                                float2* Hpart, int nchunk, cudaStream_t st);
-cudaError_t launch_k1_adj_fp32(const Geo& g, const float2* H2, const float2* coil, const float2* AT,
+cudaError_t launch_k1_adj_fp32(const Geo& g, const float2* H2, const float2* coil, const float2* A,
                                float2* xpart, int nchunk, cudaStream_t st);
 cudaError_t launch_sim_fwd(const Geo& g, const float2* x, const float2* coil, float2* V, int nchunk,
                            cudaStream_t st);
@@ -36,11 +38,11 @@ cudaError_t launch_roi_count(const Geo& g, const float2* coil, const uint8_t* ro
 cudaError_t launch_roi_scan(const int* blockcount, int* blockoff, int nblk, int* total, cudaStream_t st);
 cudaError_t launch_roi_compact(const Geo& g, const float2* coil, const uint8_t* roi, const int* blockoff,
                                int* pix, int nblk, cudaStream_t st);
-cudaError_t launch_roi_coils(const Geo& g, const float2* coil, const float2* T, const int* pix, int K, int Kpad,
-                             float2* chat, cudaStream_t st);
+cudaError_t launch_roi_coils(const Geo& g, const float2* coil, const float2* T, const int* pix, const int* dK,
+                             int Kpad, float2* chat, cudaStream_t st);
 int roi_block_pixels();
-cudaError_t launch_gram(const Geo& g, const float2* chat, const int* pix, int K, int Kpad, const int* pref,
-                        double2* P, cudaStream_t st);
+cudaError_t launch_gram(const Geo& g, const float2* chat, const int* pix, const int* dK, int Kpad,
+                        const int* pref, double2* P, cudaStream_t st);
 cudaError_t launch_hermitize(const Geo& g, double2* P, cudaStream_t st);
 cudaError_t launch_eig_init(const Geo& g, int b, double2* X, cudaStream_t st);
 cudaError_t launch_eig_matmul(const Geo& g, int b, const double2* P, const double2* X, double2* Y,

@@ -66,8 +66,48 @@ __global__ void k_make_tables(int nx, int ny, int nz, int os, float2* tw_x, floa
 cudaError_t launch_make_tables(Geo& g, float2* tw_x, float2* tw_y, float2* tw_z, float2* pre, float* ay,
                                float* az, double cycles, double kappa_y, double kappa_z, cudaStream_t st) {
   const int total = g.nx + g.ny + g.nz + 2 * g.ntx;
-  k_make_tables<<<(total + 255) / 256, 256, 0, st>>>(g.nx, g.ny, g.nz, g.os, tw_x, tw_y, tw_z, pre, ay, az,
+  note_launches(1); k_make_tables<<<(total + 255) / 256, 256, 0, st>>>(g.nx, g.ny, g.nz, g.os, tw_x, tw_y, tw_z, pre, ay, az,
                                                      cycles, kappa_y, kappa_z);
+  return cudaGetLastError();
+}
+
+// post_y[y][t] = (-1)^{m + nx/2} e^{i pi s/os} e^{-2 pi i a_y(t) y_c/ny} / sqrt(ntx)
+// post_z[z][t] = e^{-2 pi i a_z(t) z_c/nz}, t = os m + s (double precision).
+__global__ void k_make_post(int nx, int ny, int nz, int os, float2* post_y, float2* post_z, double cycles,
+                            double kappa_y, double kappa_z) {
+  const int ntx = os * nx;
+  const size_t ny_tot = (size_t)ny * ntx, total = ny_tot + (size_t)nz * ntx;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const bool isy = i < ny_tot;
+    const size_t j = isy ? i : i - ny_tot;
+    const int r = (int)(j / ntx), t = (int)(j - (size_t)r * ntx);
+    double s, c;
+    sincospi(2.0 * cycles * t / ntx, &s, &c);
+    double arg;  // in units of pi
+    float scale = 1.0f;
+    if (isy) {
+      const int m = t / os, sh = t - m * os;
+      const double ay = kappa_y * (1.0 - c) * 0.5;
+      arg = (double)sh / os - 2.0 * ay * (double)(r - ny / 2) / ny;
+      scale = (float)((((m + nx / 2) & 1) ? -1.0 : 1.0) / sqrt((double)ntx));
+    } else {
+      const double az = kappa_z * s * 0.5;
+      arg = nz > 1 ? -2.0 * az * (double)(r - nz / 2) / nz : 0.0;
+    }
+    double ps, pc;
+    sincospi(arg, &ps, &pc);
+    float2 v = make_float2((float)pc * scale, (float)ps * scale);
+    if (isy)
+      post_y[j] = v;
+    else
+      post_z[j] = v;
+  }
+}
+
+cudaError_t launch_make_post(const Geo& g, float2* post_y, float2* post_z, double cycles, double kappa_y,
+                             double kappa_z, cudaStream_t st) {
+  note_launches(1); k_make_post<<<1024, 256, 0, st>>>(g.nx, g.ny, g.nz, g.os, post_y, post_z, cycles, kappa_y,
+                                                      kappa_z);
   return cudaGetLastError();
 }
 
@@ -161,11 +201,15 @@ __global__ void k_roi_compact(Geo g, const float2* __restrict__ coil, const uint
 }
 
 // chat[n][k] = (T c)_n(r_k) / sqrt(w * sum_n |(T c)_n(r_k)|^2); zero for k >= K.
+// K = |ROI| is read on the device; rows of chat are `Kpad` apart (>= the
+// padded K), entries in [K, round_up(K, 32)) are zero.
 __global__ void k_roi_coils(Geo g, const float2* __restrict__ coil, const float2* __restrict__ T,
-                            const int* __restrict__ pix, int K, int Kpad, float2* __restrict__ chat) {
+                            const int* __restrict__ pix, const int* __restrict__ dK, int Kpad,
+                            float2* __restrict__ chat) {
   const size_t L = (size_t)g.rows * g.nx;
+  const int K = *dK;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= Kpad) return;
+  if (k >= ((K + 31) / 32) * 32) return;
   if (k >= K) {
     for (int n = 0; n < g.nc; ++n) chat[(size_t)n * Kpad + k] = make_float2(0.f, 0.f);
     return;
@@ -208,21 +252,21 @@ __global__ void k_roi_coils(Geo g, const float2* __restrict__ coil, const float2
 
 cudaError_t launch_roi_count(const Geo& g, const float2* coil, const uint8_t* roi, int* blockcount, int nblk,
                              cudaStream_t st) {
-  k_roi_count<<<nblk, kRoiThreads, 0, st>>>(g, coil, roi, blockcount);
+  note_launches(1); k_roi_count<<<nblk, kRoiThreads, 0, st>>>(g, coil, roi, blockcount);
   return cudaGetLastError();
 }
 cudaError_t launch_roi_scan(const int* blockcount, int* blockoff, int nblk, int* total, cudaStream_t st) {
-  k_roi_scan<<<1, 1024, 0, st>>>(blockcount, blockoff, nblk, total);
+  note_launches(1); k_roi_scan<<<1, 1024, 0, st>>>(blockcount, blockoff, nblk, total);
   return cudaGetLastError();
 }
 cudaError_t launch_roi_compact(const Geo& g, const float2* coil, const uint8_t* roi, const int* blockoff,
                                int* pix, int nblk, cudaStream_t st) {
-  k_roi_compact<<<nblk, kRoiThreads, 0, st>>>(g, coil, roi, blockoff, pix);
+  note_launches(1); k_roi_compact<<<nblk, kRoiThreads, 0, st>>>(g, coil, roi, blockoff, pix);
   return cudaGetLastError();
 }
-cudaError_t launch_roi_coils(const Geo& g, const float2* coil, const float2* T, const int* pix, int K, int Kpad,
-                             float2* chat, cudaStream_t st) {
-  k_roi_coils<<<(Kpad + 255) / 256, 256, 0, st>>>(g, coil, T, pix, K, Kpad, chat);
+cudaError_t launch_roi_coils(const Geo& g, const float2* coil, const float2* T, const int* pix, const int* dK,
+                             int Kpad, float2* chat, cudaStream_t st) {
+  note_launches(1); k_roi_coils<<<(Kpad + 255) / 256, 256, 0, st>>>(g, coil, T, pix, dK, Kpad, chat);
   return cudaGetLastError();
 }
 
@@ -233,8 +277,9 @@ constexpr int kGFlush = 8;     // chunks per FP32 run (256 pixels)
 constexpr int kGSlab = 2048;   // pixels per block (FP64 atomics across slabs)
 
 __global__ void __launch_bounds__(256) k_gram(Geo g, const float2* __restrict__ chat,
-                                              const int* __restrict__ pix, int K, int Kpad,
-                                              const int* __restrict__ pref, double2* __restrict__ P) {
+                                              const int* __restrict__ pix, const int* __restrict__ dK,
+                                              int Kpad, const int* __restrict__ pref,
+                                              double2* __restrict__ P) {
   extern __shared__ float2 gsm[];
   float2* As = gsm;                  // [kGKC][kGT]
   float2* Bs = As + kGKC * kGT;      // [kGKC][kGT]
@@ -250,8 +295,10 @@ __global__ void __launch_bounds__(256) k_gram(Geo g, const float2* __restrict__ 
   const int J = I + pidx;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int t0 = pref[grp] * g.w;
+  const int K = *dK;
   const int k_begin = blockIdx.z * kGSlab;
-  const int k_end = min(Kpad, k_begin + kGSlab);
+  const int k_end = min(((K + kGKC - 1) / kGKC) * kGKC, k_begin + kGSlab);
+  if (k_begin >= k_end) return;
 
   float2 acc[4][4];
   double2 acc64[4][4];
@@ -356,20 +403,20 @@ __global__ void k_hermitize(int ns, double2* P) {
   }
 }
 
-cudaError_t launch_gram(const Geo& g, const float2* chat, const int* pix, int K, int Kpad, const int* pref,
-                        double2* P, cudaStream_t st) {
+cudaError_t launch_gram(const Geo& g, const float2* chat, const int* pix, const int* dK, int Kpad,
+                        const int* pref, double2* P, cudaStream_t st) {
   const int nt = (g.ns + kGT - 1) / kGT;
   const int npairs = nt * (nt + 1) / 2;
   const int nslab = (Kpad + kGSlab - 1) / kGSlab;
   const size_t sm = sizeof(float2) * (size_t)(2 * kGKC * kGT + g.w * kGKC);
   cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_gram<<<dim3(npairs, g.G, nslab), 256, sm, st>>>(g, chat, pix, K, Kpad, pref, P);
+  note_launches(1); k_gram<<<dim3(npairs, g.G, nslab), 256, sm, st>>>(g, chat, pix, dK, Kpad, pref, P);
   return cudaGetLastError();
 }
 
 cudaError_t launch_hermitize(const Geo& g, double2* P, cudaStream_t st) {
   const int nb = (g.ns * g.ns + 255) / 256;
-  k_hermitize<<<dim3(nb < 1024 ? nb : 1024, g.G), 256, 0, st>>>(g.ns, P);
+  note_launches(1); k_hermitize<<<dim3(nb < 1024 ? nb : 1024, g.G), 256, 0, st>>>(g.ns, P);
   return cudaGetLastError();
 }
 
@@ -416,7 +463,7 @@ __global__ void k_eig_init(int ns, int b, double2* X) {
 }
 
 cudaError_t launch_eig_init(const Geo& g, int b, double2* X, cudaStream_t st) {
-  k_eig_init<<<dim3(64, g.G), 256, 0, st>>>(g.ns, b, X);
+  note_launches(1); k_eig_init<<<dim3(64, g.G), 256, 0, st>>>(g.ns, b, X);
   return cudaGetLastError();
 }
 
@@ -475,7 +522,7 @@ cudaError_t launch_eig_matmul(const Geo& g, int b, const double2* P, const doubl
                               cudaStream_t st) {
   if (b > kEigMaxB) return cudaErrorInvalidValue;
   const size_t sm = sizeof(double2) * (size_t)kMMK * b;
-  k_eig_matmul<<<dim3((g.ns + kMMRows - 1) / kMMRows, g.G), 256, sm, st>>>(g.ns, b, P, X, Y);
+  note_launches(1); k_eig_matmul<<<dim3((g.ns + kMMRows - 1) / kMMRows, g.G), 256, sm, st>>>(g.ns, b, P, X, Y);
   return cudaGetLastError();
 }
 
@@ -538,7 +585,7 @@ __global__ void __launch_bounds__(256) k_eig_orth(int ns, int b, double2* Y) {
 cudaError_t launch_eig_orth(const Geo& g, int b, double2* Y, cudaStream_t st) {
   const size_t sm = sizeof(double2) * (size_t)(g.ns + b);
   cudaFuncSetAttribute(k_eig_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_eig_orth<<<g.G, 256, sm, st>>>(g.ns, b, Y);
+  note_launches(1); k_eig_orth<<<g.G, 256, sm, st>>>(g.ns, b, Y);
   return cudaGetLastError();
 }
 
@@ -558,7 +605,7 @@ __global__ void k_eig_project(int ns, int b, const double2* __restrict__ Q, cons
 
 cudaError_t launch_eig_project(const Geo& g, int b, const double2* Q, const double2* Z, double2* Hm,
                                cudaStream_t st) {
-  k_eig_project<<<dim3((b * b + 127) / 128, g.G), 128, 0, st>>>(g.ns, b, Q, Z, Hm);
+  note_launches(1); k_eig_project<<<dim3((b * b + 127) / 128, g.G), 128, 0, st>>>(g.ns, b, Q, Z, Hm);
   return cudaGetLastError();
 }
 
@@ -709,7 +756,7 @@ cudaError_t launch_eig_jacobi(const Geo& g, int b, double2* Hm, double2* W, doub
   if (b > kEigMaxB) return cudaErrorInvalidValue;
   const size_t sm = sizeof(double2) * (size_t)b * b;
   cudaFuncSetAttribute(k_eig_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_eig_jacobi<<<g.G, 256, sm, st>>>(b, Hm, W, ritz, order, max_sweeps);
+  note_launches(1); k_eig_jacobi<<<g.G, 256, sm, st>>>(b, Hm, W, ritz, order, max_sweeps);
   return cudaGetLastError();
 }
 
@@ -731,7 +778,7 @@ __global__ void k_eig_rotate(int ns, int b, const double2* __restrict__ Q, const
 
 cudaError_t launch_eig_rotate(const Geo& g, int b, const double2* Q, const double2* W, const int* order,
                               double2* U, cudaStream_t st) {
-  k_eig_rotate<<<dim3(128, g.G), 256, 0, st>>>(g.ns, b, Q, W, order, U);
+  note_launches(1); k_eig_rotate<<<dim3(128, g.G), 256, 0, st>>>(g.ns, b, Q, W, order, U);
   return cudaGetLastError();
 }
 
@@ -762,7 +809,7 @@ __global__ void k_eig_residual(int ns, int b, const int* __restrict__ keep, cons
 
 cudaError_t launch_eig_residual(const Geo& g, int b, const double2* PU, const double2* U, const double* ritz,
                                 const int* order, double* resid, cudaStream_t st) {
-  k_eig_residual<<<g.G, 256, 0, st>>>(g.ns, b, g.keep, PU, U, ritz, order, resid);
+  note_launches(1); k_eig_residual<<<g.G, 256, 0, st>>>(g.ns, b, g.keep, PU, U, ritz, order, resid);
   return cudaGetLastError();
 }
 
@@ -813,7 +860,7 @@ __global__ void k_form_A(Geo g, int b, const double2* __restrict__ U, const floa
 
 cudaError_t launch_form_A(const Geo& g, int b, const double2* U, const float2* T, float2* A, float2* AT,
                           float* scale, cudaStream_t st) {
-  k_form_A<<<g.G, 256, 0, st>>>(g, b, U, T, A, AT, scale);
+  note_launches(1); k_form_A<<<g.G, 256, 0, st>>>(g, b, U, T, A, AT, scale);
   return cudaGetLastError();
 }
 
@@ -873,7 +920,7 @@ cudaError_t launch_compress_fp32(const Geo& g, const float2* S, int n_lines_in, 
 #define KC(J)                                                                    \
   {                                                                              \
     cudaFuncSetAttribute(k_compress_fp32<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-    k_compress_fp32<J><<<grid, 256, sm, st>>>(g, S, AT, Sc);                     \
+    note_launches(1); k_compress_fp32<J><<<grid, 256, sm, st>>>(g, S, AT, Sc);                     \
     return cudaGetLastError();                                                   \
   }
   if (need <= 1) KC(1)

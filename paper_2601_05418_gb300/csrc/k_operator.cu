@@ -28,15 +28,13 @@ constexpr int kK2Threads = 256;
 constexpr int kCB = 16;  // columns per phase-encode block
 
 // post(t) = (-1)^{m + nx/2} exp(i pi s/os) exp(-i phi(t,y,z)) / sqrt(ntx),
-// t = os m + s: the centring factor of the readout DFT times the wave PSF.
-__device__ __forceinline__ float2 readout_post(const Geo& g, int t, float yc_over_ny,
-                                               float zc_over_nz) {
-  const int m = t / g.os;
-  const int s = t - m * g.os;
-  float arg = (float)s / (float)g.os - 2.0f * (g.ay[t] * yc_over_ny + g.az[t] * zc_over_nz);
-  float2 e = expipi(arg);
-  const float sg = ((m + g.nx / 2) & 1) ? -g.inv_sqrt_ntx : g.inv_sqrt_ntx;
-  return cscale(e, sg);
+// t = os m + s: the centring factor of the readout DFT times the wave PSF,
+// from the separable tables post_y[y][t] (centring, 1/sqrt(ntx), y wave term)
+// and post_z[z][t] (z wave term).
+__device__ __forceinline__ float2 readout_post(const Geo& g, int t, int y, int z) {
+  const float2 py = g.post_y[(size_t)y * g.ntx + t];
+  if (g.nz == 1) return py;
+  return cmul(py, g.post_z[(size_t)z * g.ntx + t]);
 }
 
 struct K1Smem {
@@ -55,12 +53,10 @@ __device__ __forceinline__ K1Smem k1_smem_setup(const Geo& g, int row, float2* b
   sm.pre = base + 3 * g.ntx;
   sm.tw = base + 4 * g.ntx;
   const int y = row % g.ny, z = row / g.ny;
-  const float ycn = (float)(y - g.ny / 2) / (float)g.ny;
-  const float zcn = g.nz > 1 ? (float)(z - g.nz / 2) / (float)g.nz : 0.0f;
   for (int i = threadIdx.x; i < g.nx; i += blockDim.x) sm.tw[i] = g.tw_x[i];
   for (int i = threadIdx.x; i < g.ntx; i += blockDim.x) {
     sm.pre[i] = g.pre[i];
-    sm.post[i] = readout_post(g, i, ycn, zcn);
+    sm.post[i] = readout_post(g, i, y, z);
   }
   __syncthreads();
   return sm;
@@ -147,7 +143,7 @@ __global__ void __launch_bounds__(kK1Threads) k1_fwd_fp32(Geo g, const float2* _
 template <int MAXX>
 __global__ void __launch_bounds__(kK1Threads) k1_adj_fp32(Geo g, const float2* __restrict__ H2,
                                                           const float2* __restrict__ coil,
-                                                          const float2* __restrict__ AT,
+                                                          const float2* __restrict__ A,
                                                           float2* __restrict__ xpart, int cpc) {
   extern __shared__ float2 smem[];
   const int row = blockIdx.x, chunk = blockIdx.y;
@@ -162,17 +158,18 @@ __global__ void __launch_bounds__(kK1Threads) k1_adj_fp32(Geo g, const float2* _
   for (int j = 0; j < MAXX; ++j) xacc[j] = make_float2(0.f, 0.f);
   const int n0 = chunk * cpc;
   const int n1 = min(g.nc, n0 + cpc);
-  const int nx = g.nx, os = g.os, w = g.w;
+  const int nx = g.nx, os = g.os, w = g.w, ns = g.ns;
   for (int n = n0; n < n1; ++n) {
-    // A^H: U[t] = sum_k conj(A_g[k][n w + tau]) H2[off_p + k]
+    // A^H: U[t] = sum_k conj(A_g[k][n w + tau]) H2[off_p + k]; A is [k][i]
+    // so neighbouring t (neighbouring tau) read neighbouring addresses.
     for (int t = threadIdx.x; t < g.ntx; t += blockDim.x) {
       const int p = t / w, tau = t - p * w;
       const int gg = g.pg[p];
       const int kg = g.keep[gg];
-      const float2* Ap = AT + g.aoff[gg] + (size_t)(n * w + tau) * kg;
+      const float2* Ap = A + g.aoff[gg] + n * w + tau;
       const float2* hp = Hs + g.poff[p];
       float2 v = make_float2(0.f, 0.f);
-      for (int k = 0; k < kg; ++k) cfmac(v, __ldg(Ap + k), hp[k]);
+      for (int k = 0; k < kg; ++k) cfmac(v, __ldg(Ap + (size_t)k * ns), hp[k]);
       v = cmulc(sm.post[t], v);
       const int m = t / os, s = t - m * os;
       sm.b[s * nx + m] = v;
@@ -542,7 +539,7 @@ cudaError_t launch_k1_fwd_fp32(const Geo& g, const float2* x, const float2* coil
 #define K1F(J)                                                                               \
   {                                                                                          \
     cudaFuncSetAttribute(k1_fwd_fp32<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-    k1_fwd_fp32<J><<<grid, kK1Threads, sm, st>>>(g, x, coil, AT, Hpart, cpc);                \
+    note_launches(1); k1_fwd_fp32<J><<<grid, kK1Threads, sm, st>>>(g, x, coil, AT, Hpart, cpc);                \
     return cudaGetLastError();                                                               \
   }
   if (need <= 2) K1F(2)
@@ -555,7 +552,7 @@ cudaError_t launch_k1_fwd_fp32(const Geo& g, const float2* x, const float2* coil
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_k1_adj_fp32(const Geo& g, const float2* H2, const float2* coil, const float2* AT,
+cudaError_t launch_k1_adj_fp32(const Geo& g, const float2* H2, const float2* coil, const float2* A,
                                float2* xpart, int nchunk, cudaStream_t st) {
   const int cpc = (g.nc + nchunk - 1) / nchunk;
   dim3 grid(g.rows, nchunk);
@@ -564,7 +561,7 @@ cudaError_t launch_k1_adj_fp32(const Geo& g, const float2* H2, const float2* coi
 #define K1A(J)                                                                               \
   {                                                                                          \
     cudaFuncSetAttribute(k1_adj_fp32<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); \
-    k1_adj_fp32<J><<<grid, kK1Threads, sm, st>>>(g, H2, coil, AT, xpart, cpc);               \
+    note_launches(1); k1_adj_fp32<J><<<grid, kK1Threads, sm, st>>>(g, H2, coil, A, xpart, cpc);               \
     return cudaGetLastError();                                                               \
   }
   if (need <= 1) K1A(1)
@@ -580,7 +577,7 @@ static cudaError_t launch_sim_fwd_t(const Geo& g, const float2* x, const float2*
   dim3 grid(g.rows, nchunk);
   const size_t sm = k1_smem_bytes(g);
   cudaFuncSetAttribute(k1_sim_fwd<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k1_sim_fwd<VT><<<grid, kK1Threads, sm, st>>>(g, x, coil, V, cpc);
+  note_launches(1); k1_sim_fwd<VT><<<grid, kK1Threads, sm, st>>>(g, x, coil, V, cpc);
   return cudaGetLastError();
 }
 
@@ -592,10 +589,10 @@ static cudaError_t launch_sim_adj_t(const Geo& g, const VT* V, const float2* coi
   const size_t sm = k1_smem_bytes(g);
   if (g.nx <= kK1Threads) {
     cudaFuncSetAttribute(k1_sim_adj<VT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k1_sim_adj<VT, 1><<<grid, kK1Threads, sm, st>>>(g, V, coil, xpart, cpc);
+    note_launches(1); k1_sim_adj<VT, 1><<<grid, kK1Threads, sm, st>>>(g, V, coil, xpart, cpc);
   } else {
     cudaFuncSetAttribute(k1_sim_adj<VT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k1_sim_adj<VT, 2><<<grid, kK1Threads, sm, st>>>(g, V, coil, xpart, cpc);
+    note_launches(1); k1_sim_adj<VT, 2><<<grid, kK1Threads, sm, st>>>(g, V, coil, xpart, cpc);
   }
   return cudaGetLastError();
 }
@@ -627,15 +624,15 @@ cudaError_t launch_pe_fwd(const Geo& g, const float2* Hpart, int nchunk, int nco
   if (!g.dim3d) {
     const size_t sm = k2_smem(g.ny);
     set_k2_attr((const void*)k2_fwd_2d, sm);
-    k2_fwd_2d<<<nb, kK2Threads, sm, st>>>(g, Hpart, nchunk, ncols, Sc);
+    note_launches(1); k2_fwd_2d<<<nb, kK2Threads, sm, st>>>(g, Hpart, nchunk, ncols, Sc);
     return cudaGetLastError();
   }
   size_t sm = k2_smem(g.ny);
   set_k2_attr((const void*)k2_y_fwd3d, sm);
-  k2_y_fwd3d<<<dim3(nb, g.nz), kK2Threads, sm, st>>>(g, Hpart, nchunk, ncols, T);
+  note_launches(1); k2_y_fwd3d<<<dim3(nb, g.nz), kK2Threads, sm, st>>>(g, Hpart, nchunk, ncols, T);
   sm = k2_smem(g.nz);
   set_k2_attr((const void*)k2_z_3d, sm);
-  k2_z_3d<<<dim3(nb, g.ny), kK2Threads, sm, st>>>(g, T, Sc, ncols, 0, nullptr, nullptr, nullptr);
+  note_launches(1); k2_z_3d<<<dim3(nb, g.ny), kK2Threads, sm, st>>>(g, T, Sc, ncols, 0, nullptr, nullptr, nullptr);
   return cudaGetLastError();
 }
 
@@ -644,15 +641,15 @@ cudaError_t launch_pe_adj(const Geo& g, const float2* Sc, int ncols, float2* T, 
   if (!g.dim3d) {
     const size_t sm = k2_smem(g.ny);
     set_k2_attr((const void*)k2_adj_2d, sm);
-    k2_adj_2d<<<nb, kK2Threads, sm, st>>>(g, Sc, ncols, H);
+    note_launches(1); k2_adj_2d<<<nb, kK2Threads, sm, st>>>(g, Sc, ncols, H);
     return cudaGetLastError();
   }
   size_t sm = k2_smem(g.nz);
   set_k2_attr((const void*)k2_z_3d, sm);
-  k2_z_3d<<<dim3(nb, g.ny), kK2Threads, sm, st>>>(g, T, (float2*)Sc, ncols, 1, nullptr, nullptr, nullptr);
+  note_launches(1); k2_z_3d<<<dim3(nb, g.ny), kK2Threads, sm, st>>>(g, T, (float2*)Sc, ncols, 1, nullptr, nullptr, nullptr);
   sm = k2_smem(g.ny);
   set_k2_attr((const void*)k2_y_adj3d, sm);
-  k2_y_adj3d<<<dim3(nb, g.nz), kK2Threads, sm, st>>>(g, T, ncols, H);
+  note_launches(1); k2_y_adj3d<<<dim3(nb, g.nz), kK2Threads, sm, st>>>(g, T, ncols, H);
   return cudaGetLastError();
 }
 
@@ -667,18 +664,18 @@ cudaError_t launch_pe_normal(const Geo& g, const float2* Hpart, int nchunk, int 
   if (!g.dim3d) {
     const size_t sm = k2_smem(g.ny);
     set_k2_attr((const void*)k2_normal_2d, sm);
-    k2_normal_2d<<<nb, kK2Threads, sm, st>>>(g, Hpart, nchunk, ncols, H2, partials, counter, qq);
+    note_launches(1); k2_normal_2d<<<nb, kK2Threads, sm, st>>>(g, Hpart, nchunk, ncols, H2, partials, counter, qq);
     return cudaGetLastError();
   }
   size_t sm = k2_smem(g.ny);
   set_k2_attr((const void*)k2_y_fwd3d, sm);
-  k2_y_fwd3d<<<dim3(nb, g.nz), kK2Threads, sm, st>>>(g, Hpart, nchunk, ncols, T);
+  note_launches(1); k2_y_fwd3d<<<dim3(nb, g.nz), kK2Threads, sm, st>>>(g, Hpart, nchunk, ncols, T);
   sm = k2_smem(g.nz);
   set_k2_attr((const void*)k2_z_3d, sm);
-  k2_z_3d<<<dim3(nb, g.ny), kK2Threads, sm, st>>>(g, T, nullptr, ncols, 2, partials, counter, qq);
+  note_launches(1); k2_z_3d<<<dim3(nb, g.ny), kK2Threads, sm, st>>>(g, T, nullptr, ncols, 2, partials, counter, qq);
   sm = k2_smem(g.ny);
   set_k2_attr((const void*)k2_y_adj3d, sm);
-  k2_y_adj3d<<<dim3(nb, g.nz), kK2Threads, sm, st>>>(g, T, ncols, H2);
+  note_launches(1); k2_y_adj3d<<<dim3(nb, g.nz), kK2Threads, sm, st>>>(g, T, ncols, H2);
   return cudaGetLastError();
 }
 

@@ -40,7 +40,7 @@ __global__ void k_sum_parts(const float2* __restrict__ parts, int nchunk, size_t
 
 cudaError_t launch_sum_parts(const float2* parts, int nchunk, size_t L, float2* out, double* partials,
                              unsigned* counter, double* nrm2, cudaStream_t st) {
-  k_sum_parts<<<sum_parts_blocks(L), kVecThreads, 0, st>>>(parts, nchunk, L, out, partials, counter, nrm2);
+  note_launches(1); k_sum_parts<<<sum_parts_blocks(L), kVecThreads, 0, st>>>(parts, nchunk, L, out, partials, counter, nrm2);
   return cudaGetLastError();
 }
 
@@ -80,7 +80,7 @@ __global__ void k_cg_update1(const float2* __restrict__ parts, int nchunk, size_
 cudaError_t launch_cg_update1(const float2* parts, int nchunk, size_t L, float2* x, float2* r, const float2* p,
                               const double* rr, const double* qq, double* partials, unsigned* counter,
                               double* rr_new, double* hist, int* status, cudaStream_t st) {
-  k_cg_update1<<<sum_parts_blocks(L), kVecThreads, 0, st>>>(parts, nchunk, L, x, r, p, rr, qq, partials,
+  note_launches(1); k_cg_update1<<<sum_parts_blocks(L), kVecThreads, 0, st>>>(parts, nchunk, L, x, r, p, rr, qq, partials,
                                                             counter, rr_new, hist, status);
   return cudaGetLastError();
 }
@@ -104,7 +104,7 @@ __global__ void k_cg_update2(float2* __restrict__ p, const float2* __restrict__ 
 
 cudaError_t launch_cg_update2(float2* p, const float2* r, size_t L, const double* rr, const double* rr_new,
                               cudaStream_t st) {
-  k_cg_update2<<<sum_parts_blocks(L), kVecThreads, 0, st>>>(p, r, L, rr, rr_new);
+  note_launches(1); k_cg_update2<<<sum_parts_blocks(L), kVecThreads, 0, st>>>(p, r, L, rr, rr_new);
   return cudaGetLastError();
 }
 
@@ -119,7 +119,7 @@ __global__ void k_axpby(float2* __restrict__ y, const float2* __restrict__ a, co
 
 cudaError_t launch_axpby(float2* y, const float2* a, const float2* b, float alpha, float beta, size_t L,
                          cudaStream_t st) {
-  k_axpby<<<sum_parts_blocks(L), kVecThreads, 0, st>>>(y, a, b, alpha, beta, L);
+  note_launches(1); k_axpby<<<sum_parts_blocks(L), kVecThreads, 0, st>>>(y, a, b, alpha, beta, L);
   return cudaGetLastError();
 }
 
@@ -135,13 +135,13 @@ __global__ void k_scale_by(float2* __restrict__ v, const float2* __restrict__ sr
 
 cudaError_t launch_scale_by(float2* v, const float2* src, const double* nrm2, size_t L, double* Lout,
                             cudaStream_t st) {
-  k_scale_by<<<sum_parts_blocks(L), kVecThreads, 0, st>>>(v, src, nrm2, L, Lout);
+  note_launches(1); k_scale_by<<<sum_parts_blocks(L), kVecThreads, 0, st>>>(v, src, nrm2, L, Lout);
   return cudaGetLastError();
 }
 
 __global__ void k_set_scalar(double* d, double v) { *d = v; }
 cudaError_t launch_set_scalar(double* d, double v, cudaStream_t st) {
-  k_set_scalar<<<1, 1, 0, st>>>(d, v);
+  note_launches(1); k_set_scalar<<<1, 1, 0, st>>>(d, v);
   return cudaGetLastError();
 }
 
@@ -154,11 +154,11 @@ __global__ void k_zero(float2* __restrict__ d, size_t n) {
     d[i] = make_float2(0.f, 0.f);
 }
 cudaError_t launch_copy(float2* dst, const float2* src, size_t n, cudaStream_t st) {
-  k_copy<<<sum_parts_blocks(n), kVecThreads, 0, st>>>(dst, src, n);
+  note_launches(1); k_copy<<<sum_parts_blocks(n), kVecThreads, 0, st>>>(dst, src, n);
   return cudaGetLastError();
 }
 cudaError_t launch_zero(float2* dst, size_t n, cudaStream_t st) {
-  k_zero<<<sum_parts_blocks(n), kVecThreads, 0, st>>>(dst, n);
+  note_launches(1); k_zero<<<sum_parts_blocks(n), kVecThreads, 0, st>>>(dst, n);
   return cudaGetLastError();
 }
 
@@ -257,7 +257,7 @@ cudaError_t launch_fista_step(const Geo& g, const float2* parts, int nchunk, flo
                               int* status, cudaStream_t st) {
   const int ts = 1 << levels;
   const int ntiles = (g.nx / ts) * (g.ny / ts) * g.nz;
-  k_fista_step<<<ntiles, 256, 0, st>>>(g, parts, nchunk, x, y, b, Lip, (float)lam, levels, (float)ck, status);
+  note_launches(1); k_fista_step<<<ntiles, 256, 0, st>>>(g, parts, nchunk, x, y, b, Lip, (float)lam, levels, (float)ck, status);
   return cudaGetLastError();
 }
 

@@ -75,7 +75,11 @@ _sig("gpjc_plan_destroy", [_P], None)
 _sig("gpjc_plan_ntx_c", [_P, _I32P])
 _sig("gpjc_plan_tables", [_P, _I32P, _I32P, _I32P])
 _sig("gpjc_build_groups", [_P, _P, _P, _P, C.POINTER(BuildParams), _P, C.POINTER(_P)])
+_sig("gpjc_groups_rebuild", [_P, _P, _P, _P, _P])
 _sig("gpjc_groups_from_matrices", [_P, _P, C.POINTER(_P)])
+_sig("gpjc_launch_count", [], C.c_uint64)
+_sig("gpjc_op_profile", [_P, C.c_int32])
+_sig("gpjc_op_profile_read", [_P, C.c_int32, C.POINTER(C.c_double), _I32P])
 _sig("gpjc_groups_destroy", [_P], None)
 _sig("gpjc_groups_info_get", [_P, C.POINTER(GroupsInfo)])
 _sig("gpjc_groups_get", [_P, _P, _P])
@@ -105,6 +109,14 @@ def lib():
 
 def version() -> str:
     return _lib.gpjc_version().decode()
+
+
+def launch_count() -> int:
+    """Kernels launched by libgpjc so far in this process."""
+    return int(_lib.gpjc_launch_count())
+
+
+STAGE_READOUT_FWD, STAGE_PHASE_ENCODE, STAGE_READOUT_ADJ = 0, 1, 2
 
 
 def _stream(stream=None):
@@ -181,6 +193,16 @@ class Groups:
         check(_lib.gpjc_build_groups(plan.h, _dptr(coil, torch.complex64), _dptr(roi, torch.uint8), Tp,
                                      C.byref(bp), _stream(stream), C.byref(h)))
         return cls(plan, h)
+
+    def rebuild(self, coil: torch.Tensor, roi: torch.Tensor, T: Optional[np.ndarray] = None, stream=None):
+        """Recompute in place from new coil maps / ROI (asynchronous, no allocation)."""
+        Tp = None
+        if T is not None:
+            self._T = np.ascontiguousarray(np.asarray(T, np.complex64))
+            Tp = self._T.ctypes.data_as(_P)
+        check(_lib.gpjc_groups_rebuild(self.h, _dptr(coil, torch.complex64), _dptr(roi, torch.uint8), Tp,
+                                       _stream(stream)))
+        return self
 
     @classmethod
     def from_matrices(cls, plan: Plan, As: Sequence[np.ndarray]) -> "Groups":
@@ -260,6 +282,15 @@ class Operator:
     @property
     def data_shape(self):
         return (self.plan.geom.n_lines, self.plan.ntx_c)
+
+    def profile(self, enable: bool = True) -> None:
+        check(_lib.gpjc_op_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, stage: int):
+        """(total device ms, launches) of a stage since the last reset."""
+        ms, n = C.c_double(), C.c_int32()
+        check(_lib.gpjc_op_profile_read(self.h, stage, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
 
     def autotune(self, stream=None) -> int:
         n = C.c_int32()
