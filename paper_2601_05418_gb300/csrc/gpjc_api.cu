@@ -552,10 +552,12 @@ static void prof_begin(gpjc_op* op, int stage, cudaStream_t st, size_t* mark) {
   *mark = op->prof_used;
   op->prof_used += 2;
   op->prof_marks.push_back({stage, *mark});
-  cudaEventRecord(op->prof_pool[*mark], st);
+  // inside a capture the record must become an event node of the graph
+  cudaEventRecordWithFlags(op->prof_pool[*mark], st, g_capturing ? cudaEventRecordExternal : 0);
 }
 static void prof_end(gpjc_op* op, cudaStream_t st, size_t mark) {
-  if (mark != (size_t)-1) cudaEventRecord(op->prof_pool[mark + 1], st);
+  if (mark != (size_t)-1)
+    cudaEventRecordWithFlags(op->prof_pool[mark + 1], st, g_capturing ? cudaEventRecordExternal : 0);
 }
 
 static int auto_nchunk(const gpjc_plan* p) {
