@@ -213,6 +213,29 @@ typedef struct gpjc_recon_info {
 gpjc_status gpjc_recon(const gpjc_op* op, const float* d_Sc, float* d_x, const gpjc_recon_params* params,
                        gpjc_recon_info* info, void* stream);
 
+/* ------------------------------------------------------------------ no allocation -- */
+/* x = E_c^H y without any allocation: the paper has no counterpart; this
+ * entry point exists for callers that cannot call cudaMalloc on the path
+ * where they apply the adjoint -- for example code that runs inside a
+ * component that forbids device allocation after start-up (cudaMalloc and
+ * cudaFree synchronise the device and can fail under a fixed memory budget),
+ * so it cannot create the workspace of a gpjc_op.  It needs only `groups`
+ * (and its plan), created once at start-up, and the caller's buffers:
+ *   d_coil [nc][nz][ny][nx], d_y [n_lines][ntx_c] in, d_x [nz][ny][nx] out
+ *   (complex64, device), with the same layouts and result as gpjc_apply_EH.
+ * Scratch: a static 32 MiB device array inside the library, held on every
+ * GPU that loads the library until the process exits; geometries whose
+ * hybrid matrix (rows x ntx_c complex64, twice that in 3D) exceeds it are
+ * rejected with GPJC_EINVAL before any launch.  Calls allocate nothing and
+ * free nothing.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current: make that first
+ * call before any stream capture.  Every call on a device shares the one
+ * array and overwrites all of it that it reads, so no state carries over;
+ * calls whose execution overlaps on the GPU (other streams, other threads)
+ * race on it and must be serialised by the caller. */
+gpjc_status gpjc_apply_EH_static(const gpjc_groups* groups, const float* d_coil, const float* d_y, float* d_x,
+                                 void* stream);
+
 /* ------------------------------------------------------------------ profiling -- */
 /* Kernels launched by this library in this process (graph replays add the
  * kernel nodes of the replayed graph).  Thread-safe. */

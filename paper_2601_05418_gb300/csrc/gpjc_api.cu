@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -959,5 +960,47 @@ extern "C" gpjc_status gpjc_op_profile_read(const gpjc_op* op, int32_t stage, do
   }
   *total_ms = tot;
   *count = n;
+  return GPJC_OK;
+}
+
+// ------------------------------------------------------------------ no-allocation adjoint --
+// A variant of gpjc_apply_EH whose scratch (the hybrid matrix, and in 3D the
+// phase-encode intermediate) lives in a fixed device array of this library
+// instead of an operator workspace, so a call allocates nothing.
+static constexpr size_t kStaticScratchBytes = (size_t)32 << 20;  // 32 MiB on every device that loads the library
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+static std::mutex g_static_mu;
+static void* g_static_addr[256];  // per device ordinal, filled on the first call on that device
+
+extern "C" gpjc_status gpjc_apply_EH_static(const gpjc_groups* gr, const float* d_coil, const float* d_y,
+                                            float* d_x, void* stream) {
+  if (!gr || !d_coil || !d_y || !d_x) return fail(GPJC_EINVAL, "null argument");
+  const Geo& g = gr->plan->geo;
+  const size_t hybrid = sizeof(float2) * (size_t)g.rows * g.ntxc;
+  const size_t need = g.dim3d ? 2 * hybrid : hybrid;
+  if (need > kStaticScratchBytes)
+    return fail(GPJC_EINVAL, "gpjc_apply_EH_static needs %zu bytes of scratch; its static scratch holds %zu",
+                need, kStaticScratchBytes);
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(GPJC_EUNSUPPORTED, "device ordinal %d out of range", dev);
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(GPJC_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+      g_static_addr[dev] = p;
+    }
+    base = g_static_addr[dev];
+  }
+  float2* H2 = (float2*)base;
+  float2* T = g.dim3d ? H2 + (size_t)g.rows * g.ntxc : nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  // H2 and T are fully overwritten before they are read: nothing to clear.
+  CK(launch_pe_adj(g, (const float2*)d_y, g.ntxc, T, H2, st));
+  CK(launch_k1_adj_fp32(g, H2, (const float2*)d_coil, gr->A, (float2*)d_x, 1, st));
   return GPJC_OK;
 }

@@ -95,6 +95,7 @@ _sig("gpjc_apply_normal", [_P, _P, _P, _P, _P])
 _sig("gpjc_simulate", [_P, _P, _P, _P])
 _sig("gpjc_simulate_adjoint", [_P, _P, _P, _P])
 _sig("gpjc_recon", [_P, _P, _P, C.POINTER(ReconParams), C.POINTER(ReconInfo), _P])
+_sig("gpjc_apply_EH_static", [_P, _P, _P, _P, _P])
 
 
 def check(status: int) -> None:
@@ -347,6 +348,17 @@ class Operator:
         check(_lib.gpjc_recon(self.h, _dptr(Sc, torch.complex64), _dptr(out, torch.complex64), C.byref(rp),
                               C.byref(info) if sync else None, _stream(stream)))
         return out, {"status": info.status, "lipschitz": info.lipschitz, "history": hist}
+
+
+def apply_EH_static(groups: Groups, coil: torch.Tensor, y: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+    """E_c^H y with the library's static scratch: no operator, no allocation
+    inside the call (for callers that cannot allocate device memory there)."""
+    g = groups.plan.geom
+    if out is None:
+        out = torch.empty((g.nz, g.ny, g.nx), dtype=torch.complex64, device=y.device)
+    check(_lib.gpjc_apply_EH_static(groups.h, _dptr(coil, torch.complex64), _dptr(y, torch.complex64),
+                                    _dptr(out, torch.complex64), _stream(stream)))
+    return out
 
 
 def plan_from(geom) -> Plan:
