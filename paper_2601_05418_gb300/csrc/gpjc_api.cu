@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -128,6 +129,7 @@ struct gpjc_plan {
   std::vector<int> pg, keep, poff, ref, aoff, line_ky, line_kz, line_of;
   std::vector<int> out_tbase, out_abase, out_astride;
   Geo geo;
+  RTiles rt_f, rt_a;  // register-tiled readout stage (rb == 0: use the per-output kernels)
   DevMem mem;
 };
 
@@ -255,6 +257,39 @@ extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
   g.tw_x = tw_x; g.tw_y = tw_y; g.tw_z = tw_z; g.pre = pre; g.post_y = post_y; g.post_z = post_z;
   CK(launch_make_tables(g, tw_x, tw_y, tw_z, pre, ay, az, p->cycles, p->kappa_y, p->kappa_z, 0));
   CK(launch_make_post(g, post_y, post_z, p->cycles, p->kappa_y, p->kappa_z, 0));
+  // register-tile tables of the readout stage: the smallest rows-per-block
+  // that gives every thread of a block a tile, within the shared-memory and
+  // register budgets
+  {
+    ReadoutGeomHost rh;
+    rh.G = G; rh.w = w; rh.ntx = (int)ntx; rh.ntxc = p->ntxc;
+    rh.pg = p->pg; rh.keep = p->keep; rh.poff = p->poff; rh.aoff = p->aoff;
+    for (int adj = 0; adj < 2; ++adj) {
+      int best = 0;
+      for (int rb = 1; rb <= 8; rb *= 2) {
+        const int nt = readout_tile_count(rh, rb, adj != 0);
+        const size_t smem = adj ? readout_adj_smem(g, rb) : readout_fwd_smem(g, rb);
+        if (smem > 110 * 1024 || (nt + 255) / 256 > (adj ? 4 : 3) || rb > g.rows) break;
+        if (adj && (rb * nx + 255) / 256 > 8) break;
+        best = rb;
+        if (nt >= 256) break;
+      }
+      RTiles& rt = adj ? p->rt_a : p->rt_f;
+      rt.rb = best;
+      rt.nt = 0;
+      rt.hdr = nullptr;
+      rt.cols = nullptr;
+      if (best) {
+        std::vector<int4> hdr, cols;
+        build_readout_tiles(rh, best, adj != 0, &hdr, &cols);
+        int4 *dh, *dc;
+        if ((s = m.upload(&dh, hdr)) || (s = m.upload(&dc, cols))) return s;
+        rt.nt = (int)hdr.size();
+        rt.hdr = dh;
+        rt.cols = dc;
+      }
+    }
+  }
   CK(cudaDeviceSynchronize());
   *out = guard.release();
   return GPJC_OK;
@@ -539,6 +574,7 @@ struct gpjc_op {
   int graph_kernels;
   cudaStream_t cap_st;
   cudaEvent_t ev_in, ev_out;
+  bool legacy_readout;  // use the per-output readout kernels (set by GPJC_LEGACY_READOUT=1)
   // optional per-stage timing with events (GPJC_STAGE_*)
   bool prof_on;
   std::vector<cudaEvent_t> prof_pool;
@@ -617,6 +653,10 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   op->V = op->TV = nullptr;
   op->gexec = nullptr;
   op->graph_kernels = 0;
+  {
+    const char* e = getenv("GPJC_LEGACY_READOUT");
+    op->legacy_readout = e && e[0] == '1';
+  }
   op->prof_on = false;
   op->prof_used = 0;
   op->cap_st = nullptr;
@@ -642,12 +682,27 @@ extern "C" void gpjc_op_destroy(gpjc_op* op) {
 }
 
 // --- internal launch sequences (no validation) ---
+// readout stage of E_c into op->Hpart (register-tiled kernel when the plan has tiles)
+static cudaError_t readout_fwd(const gpjc_op* op, const float2* x, cudaStream_t st) {
+  const gpjc_plan* p = op->plan;
+  if (p->rt_f.rb && !op->legacy_readout)
+    return launch_k1f_tiled(p->geo, p->rt_f, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st);
+  return launch_k1_fwd_fp32(p->geo, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st);
+}
+// readout stage of E_c^H from op->H2 into op->xparts
+static cudaError_t readout_adj(const gpjc_op* op, cudaStream_t st) {
+  const gpjc_plan* p = op->plan;
+  if (p->rt_a.rb && !op->legacy_readout)
+    return launch_k1a_tiled(p->geo, p->rt_a, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st);
+  return launch_k1_adj_fp32(p->geo, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st);
+}
+
 static gpjc_status op_fwd(const gpjc_op* cop, const float2* x, float2* y, cudaStream_t st) {
   gpjc_op* op = const_cast<gpjc_op*>(cop);
   const Geo& g = op->plan->geo;
   size_t m;
   prof_begin(op, GPJC_STAGE_READOUT_FWD, st, &m);
-  CK(launch_k1_fwd_fp32(g, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st));
+  CK(readout_fwd(op, x, st));
   prof_end(op, st, m);
   prof_begin(op, GPJC_STAGE_PHASE_ENCODE, st, &m);
   CK(launch_pe_fwd(g, op->Hpart, op->nchunk, g.ntxc, op->T, y, st));
@@ -663,7 +718,7 @@ static gpjc_status op_adj_parts(const gpjc_op* cop, const float2* y, cudaStream_
   CK(launch_pe_adj(g, y, g.ntxc, op->T, op->H2, st));
   prof_end(op, st, m);
   prof_begin(op, GPJC_STAGE_READOUT_ADJ, st, &m);
-  CK(launch_k1_adj_fp32(g, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st));
+  CK(readout_adj(op, st));
   prof_end(op, st, m);
   return GPJC_OK;
 }
@@ -674,13 +729,13 @@ static gpjc_status op_normal_parts(const gpjc_op* cop, const float2* x, double* 
   const Geo& g = op->plan->geo;
   size_t m;
   prof_begin(op, GPJC_STAGE_READOUT_FWD, st, &m);
-  CK(launch_k1_fwd_fp32(g, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st));
+  CK(readout_fwd(op, x, st));
   prof_end(op, st, m);
   prof_begin(op, GPJC_STAGE_PHASE_ENCODE, st, &m);
   CK(launch_pe_normal(g, op->Hpart, op->nchunk, g.ntxc, op->T, op->H2, op->partials, op->counter, qq, st));
   prof_end(op, st, m);
   prof_begin(op, GPJC_STAGE_READOUT_ADJ, st, &m);
-  CK(launch_k1_adj_fp32(g, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st));
+  CK(readout_adj(op, st));
   prof_end(op, st, m);
   return GPJC_OK;
 }

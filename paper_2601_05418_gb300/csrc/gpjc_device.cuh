@@ -133,9 +133,16 @@ __device__ __forceinline__ void dft7(float2* v) {
   dft_odd<7, SIGN>(v, c, s);
 }
 
+// Shared-memory index with one padding slot every 8 complex values: keeps
+// the stride-R stores of the first Stockham stages (R = 2..8) and the
+// stride-8 pattern after a radix-8 stage free of bank conflicts.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int spad_size(int n) { return n + (n >> 3) + 1; }
+
 // One Stockham stage of radix R on `batch` contiguous transforms of length n.
-// tw[k] = exp(-2 pi i k / n) for k < n.
-template <int R, int SIGN>
+// tw[k] = exp(-2 pi i k / n) for k < n.  With PAD, element i of the logical
+// buffer lives at spad(i).
+template <int R, int SIGN, bool PAD = false>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, float2* __restrict__ dst,
                                                int n, int batch, int bs, int ns,
                                                const float2* __restrict__ tw, int tid, int nthr) {
@@ -145,13 +152,13 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
   for (int idx = tid; idx < total; idx += nthr) {
     const int f = idx / m;
     const int j = idx - f * m;
-    const float2* s = src + f * bs;
-    float2* d = dst + f * bs;
+    const int sb = f * bs;
     float2 v[R];
     const int k = j % ns;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      float2 a = s[j + r * m];
+      const int li = sb + j + r * m;
+      float2 a = src[PAD ? spad(li) : li];
       if (r > 0 && k > 0) {
         const int e = k * r * twstep;  // < n since k < ns and r < R
         float2 w = tw[e];
@@ -166,9 +173,12 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
     if (R == 5) dft5<SIGN>(v);
     if (R == 7) dft7<SIGN>(v);
     if (R == 8) dft8<SIGN>(v);
-    const int base = (j / ns) * ns * R + k;
+    const int base = sb + (j / ns) * ns * R + k;
 #pragma unroll
-    for (int q = 0; q < R; ++q) d[base + q * ns] = v[q];
+    for (int q = 0; q < R; ++q) {
+      const int lo = base + q * ns;
+      dst[PAD ? spad(lo) : lo] = v[q];
+    }
   }
 }
 
@@ -176,19 +186,19 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
 // are `bs` elements apart.  Data starts in `a`; returns the buffer holding
 // the result (a or b).  SIGN = -1 forward, +1 inverse.  Must be called by
 // all threads of the block; ends with __syncthreads().
-template <int SIGN>
+template <int SIGN, bool PAD = false>
 __device__ float2* fft_batch(float2* a, float2* b, int batch, int bs, const FftPlan& pl,
                              const float2* __restrict__ tw, int tid, int nthr) {
   int ns = 1;
   for (int st = 0; st < pl.nst; ++st) {
     const int R = pl.rad[st];
     switch (R) {
-      case 2: stockham_stage<2, SIGN>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
-      case 3: stockham_stage<3, SIGN>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
-      case 4: stockham_stage<4, SIGN>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
-      case 5: stockham_stage<5, SIGN>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
-      case 7: stockham_stage<7, SIGN>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
-      default: stockham_stage<8, SIGN>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
+      case 2: stockham_stage<2, SIGN, PAD>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
+      case 3: stockham_stage<3, SIGN, PAD>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
+      case 4: stockham_stage<4, SIGN, PAD>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
+      case 5: stockham_stage<5, SIGN, PAD>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
+      case 7: stockham_stage<7, SIGN, PAD>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
+      default: stockham_stage<8, SIGN, PAD>(a, b, pl.n, batch, bs, ns, tw, tid, nthr); break;
     }
     __syncthreads();
     float2* t = a;

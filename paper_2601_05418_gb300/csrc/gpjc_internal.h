@@ -42,6 +42,18 @@ struct Geo {
   const float2* post_z;   // [nz][ntx] e^{-2 pi i a_z(t) z_c/nz}
 };
 
+// Register-tile tables of the readout stage (k_readout.cu).  rb rows per
+// block; forward tiles: hdr = (aoff_g + k0, keep_g, kept count, 0), cols =
+// (r * stride + p w, r * ntxc + off_p + k0) or (-1, -1); adjoint tiles:
+// hdr = (aoff_g + tau0, keep_g, sample count, 0), cols = (r, off_p,
+// p w + tau0, 0) or (-1, ...).
+struct RTiles {
+  int rb;
+  int nt;
+  const int4* hdr;   // [nt]
+  const int4* cols;  // [nt * 4]
+};
+
 // Device status word values (written by kernels, read by the host).
 enum DevStatus : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2, kDevBadIndex = 3 };
 

@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "gpjc_internal.h"
 
 namespace gpjc {
@@ -31,6 +33,21 @@ cudaError_t launch_pe_adj(const Geo& g, const float2* Sc, int ncols, float2* T, 
 cudaError_t launch_pe_normal(const Geo& g, const float2* Hpart, int nchunk, int ncols, float2* T, float2* H2,
                              double* partials, unsigned* counter, double* qq, cudaStream_t st);
 int pe_normal_blocks(const Geo& g, int ncols);
+
+// ---- register-tiled readout stage (k_readout.cu)
+struct ReadoutGeomHost {
+  int G, w, ntx, ntxc;
+  std::vector<int> pg, keep, poff, aoff;
+};
+void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, std::vector<int4>* hdr,
+                         std::vector<int4>* cols);
+int readout_tile_count(const ReadoutGeomHost& h, int rb, bool adjoint);
+size_t readout_fwd_smem(const Geo& g, int rb);
+size_t readout_adj_smem(const Geo& g, int rb);
+cudaError_t launch_k1f_tiled(const Geo& g, const RTiles& tl, const float2* x, const float2* coil,
+                             const float2* AT, float2* Hpart, int nchunk, cudaStream_t st);
+cudaError_t launch_k1a_tiled(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,
+                             const float2* A, float2* xpart, int nchunk, cudaStream_t st);
 
 // ---- groups (k_groups.cu)
 cudaError_t launch_roi_count(const Geo& g, const float2* coil, const uint8_t* roi, int* blockcount, int nblk,
