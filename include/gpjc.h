@@ -59,7 +59,8 @@ typedef enum gpjc_status {
 
 typedef enum gpjc_precision {
   GPJC_FP32 = 0, /* FP32 data and FFMA compression */
-  GPJC_BF16 = 1  /* BF16 operands on tensor cores, FP32 accumulation, per-group scale */
+  GPJC_BF16 = 1, /* BF16 operands on tensor cores (tcgen05), FP32 accumulation, per-group scale */
+  GPJC_FP16 = 2  /* FP16 operands on tensor cores (tcgen05), FP32 accumulation, per-group scale */
 } gpjc_precision;
 
 /* Geometry of one slice or volume.  All arrays are host memory, copied by
@@ -157,8 +158,12 @@ gpjc_status gpjc_groups_roi(const gpjc_groups* groups, int32_t* h_pix);
 
 /* ------------------------------------------------------------------ compress -- */
 /* S'_{l,p} = A_{g(p)} s_{l,p} for every line and patch (Eq. 13).
- *   d_S  [n_lines][nc][ntx] complex64 raw data, device
- *   d_Sc [n_lines][ntx_c]  complex64 output, device */
+ *   d_S  [n_lines][nc][ntx] complex64 raw data, device (16-byte aligned for BF16 / FP16)
+ *   d_Sc [n_lines][ntx_c]  complex64 output, device
+ * GPJC_FP32 contracts in FP32; GPJC_BF16 / GPJC_FP16 stage patch tiles with
+ * TMA, round to 16 bits and run the group GEMMs on the tensor cores (FP32
+ * accumulation); they need a periodic group map (patch p in group p mod G,
+ * G w dividing ntx), else GPJC_EUNSUPPORTED. */
 gpjc_status gpjc_compress(const gpjc_groups* groups, const float* d_S, float* d_Sc, gpjc_precision prec,
                           void* stream);
 
@@ -166,6 +171,9 @@ gpjc_status gpjc_compress(const gpjc_groups* groups, const float* d_S, float* d_
 /* Binds groups and coil maps (d_coil is referenced, not copied: it must stay
  * valid and unchanged while the operator lives) and allocates the
  * workspaces.  nchunk: coil chunks of the readout stage (0 = automatic).
+ * prec: GPJC_FP32 applies A_g with FP32 FFMA inside the fused readout
+ * kernels; GPJC_BF16 / GPJC_FP16 write the readout spectra as 16-bit hybrid
+ * data and apply A_g / A_g^H as tensor-core GEMMs (periodic group maps).
  * Synchronous. */
 gpjc_status gpjc_op_create(const gpjc_groups* groups, const float* d_coil, gpjc_precision prec, int32_t nchunk,
                            gpjc_op** out);

@@ -130,8 +130,47 @@ struct gpjc_plan {
   std::vector<int> out_tbase, out_abase, out_astride;
   Geo geo;
   RTiles rt_f, rt_a;  // register-tiled readout stage (rb == 0: use the per-output kernels)
+  bool tc_ok;          // tensor-core compression available (periodic group map, sizes in range)
+  TcGeom tc32, tc16;   // for FP32 sources (raw data) and 16-bit sources (hybrid data)
   DevMem mem;
 };
+
+// Tensor-core compression geometry for sources of `ebytes` bytes per real
+// element; false when the group map or the sizes do not fit the kernels.
+static bool make_tc_geom(const gpjc_plan* p, int ebytes, TcGeom* t) {
+  memset(t, 0, sizeof *t);
+  const int G = p->G, w = p->w;
+  const long long P = (long long)G * w;
+  if (p->ntx % P) return false;
+  for (int q = 0; q < p->np; ++q)
+    if (p->pg[q] != q % G) return false;
+  const int n_occ = (int)(p->ntx / P);
+  if (128 % n_occ) return false;
+  if (p->keep_max > 128 || w > 64) return false;
+  if (((long long)P * ebytes) % 8 || ((long long)p->ntx * ebytes) % 8) return false;
+  t->G = G; t->w = w; t->nc = p->nc; t->ns = p->ns; t->ntx = p->ntx; t->ntxc = p->ntxc;
+  t->n_occ = n_occ; t->P = (int)P; t->lt = 128 / n_occ;
+  int c0 = 1;
+  while ((2 * w * c0) % 16) ++c0;
+  int ncc = c0;
+  while (ncc + c0 <= p->nc && 2 * w * (ncc + c0) <= 128) ncc += c0;
+  t->ncc = ncc;
+  t->nchunks = (p->nc + ncc - 1) / ncc;
+  t->Kc = 2 * w * ncc;
+  t->npad = ((2 * p->keep_max + 15) / 16) * 16;
+  t->xalign = 16 / ebytes;
+  t->box0 = ((2 * w + t->xalign - 2 + t->xalign - 1) / t->xalign) * t->xalign;
+  t->stg_tx = t->box0 * n_occ * ncc * t->lt * ebytes;
+  t->stg_bytes = ((t->stg_tx + 1023) / 1024) * 1024;
+  int tc = 32;
+  while (tc < t->npad) tc *= 2;
+  t->tmem_cols = tc;
+  t->Kx = ((2 * p->keep_max + 15) / 16) * 16;
+  t->nexp = ((2 * p->ns + 15) / 16) * 16;
+  if (t->box0 > 256 || ncc > 256 || t->lt > 256 || n_occ > 256) return false;
+  if (tc_compress_smem(*t) > 220 * 1024 || tc_expand_smem(*t) > 220 * 1024) return false;
+  return true;
+}
 
 extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
   if (!gm || !out) return fail(GPJC_EINVAL, "null geometry or output pointer");
@@ -257,6 +296,12 @@ extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
   g.tw_x = tw_x; g.tw_y = tw_y; g.tw_z = tw_z; g.pre = pre; g.post_y = post_y; g.post_z = post_z;
   CK(launch_make_tables(g, tw_x, tw_y, tw_z, pre, ay, az, p->cycles, p->kappa_y, p->kappa_z, 0));
   CK(launch_make_post(g, post_y, post_z, p->cycles, p->kappa_y, p->kappa_z, 0));
+  p->tc_ok = make_tc_geom(p, 4, &p->tc32) && make_tc_geom(p, 2, &p->tc16);
+  if (p->tc_ok) {
+    p->tc32.keep = p->tc16.keep = d_keep;
+    p->tc32.aoff = p->tc16.aoff = d_aoff;
+    p->tc32.poff = p->tc16.poff = d_poff;
+  }
   // register-tile tables of the readout stage: the smallest rows-per-block
   // that gives every thread of a block a tile, within the shared-memory and
   // register budgets
@@ -330,6 +375,11 @@ struct gpjc_groups {
   double2 *X, *Y, *U, *Hm, *W;
   double *ritz, *resid;
   int* order;
+  // tensor-core packs of A_g (index 0: FP16, 1: BF16): compression B per
+  // (group, coil chunk) and expansion B per group; refreshed on every build
+  uint16_t* tc_bc[2];
+  uint16_t* tc_bx[2];
+  int* tc_status;
   // host copies, read lazily
   mutable bool host_valid;
   mutable long long K;
@@ -344,6 +394,26 @@ static gpjc_status groups_alloc_A(gpjc_groups* gr) {
   gpjc_status s;
   if ((s = gr->mem.alloc(&gr->A, na)) || (s = gr->mem.alloc(&gr->AT, na)) || (s = gr->mem.alloc(&gr->scale, p->G)))
     return s;
+  gr->tc_bc[0] = gr->tc_bc[1] = gr->tc_bx[0] = gr->tc_bx[1] = nullptr;
+  gr->tc_status = nullptr;
+  if (p->tc_ok) {
+    const TcGeom& t = p->tc16;
+    const size_t nbc = (size_t)p->G * t.nchunks * t.npad * t.Kc, nbx = (size_t)p->G * t.nexp * t.Kx;
+    for (int f = 0; f < 2; ++f)
+      if ((s = gr->mem.alloc(&gr->tc_bc[f], nbc)) || (s = gr->mem.alloc(&gr->tc_bx[f], nbx))) return s;
+    if ((s = gr->mem.alloc(&gr->tc_status, 1))) return s;
+    CK(cudaMemset(gr->tc_status, 0, sizeof(int)));
+  }
+  return GPJC_OK;
+}
+
+// re-packs the tensor-core images of A_g after A changed
+static gpjc_status groups_pack_tc(gpjc_groups* gr, cudaStream_t st) {
+  const gpjc_plan* p = gr->plan;
+  if (!p->tc_ok) return GPJC_OK;
+  TcGeom t = p->tc16;  // the packs depend only on N, K and chunking, shared by both sources
+  t.scale = gr->scale;
+  for (int f = 0; f < 2; ++f) CK(launch_tc_pack(t, f, gr->A, gr->scale, gr->tc_bc[f], gr->tc_bx[f], st));
   return GPJC_OK;
 }
 
@@ -376,7 +446,7 @@ static gpjc_status groups_compute(gpjc_groups* gr, const float2* coil, const uin
   CK(launch_eig_residual(g, b, Y, gr->U, gr->ritz, gr->order, gr->resid, st));
   CK(launch_form_A(g, b, gr->U, h_T ? gr->dT : nullptr, gr->A, gr->AT, gr->scale, st));
   gr->host_valid = false;
-  return GPJC_OK;
+  return groups_pack_tc(gr, st);
 }
 
 // Reads |ROI|, Ritz values and residuals back (synchronous).
@@ -490,6 +560,8 @@ extern "C" gpjc_status gpjc_groups_from_matrices(const gpjc_plan* plan, const fl
   CK(cudaMemcpy(gr->A, hA.data(), sizeof(float2) * na, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(gr->AT, hAT.data(), sizeof(float2) * na, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(gr->scale, sc.data(), sizeof(float) * sc.size(), cudaMemcpyHostToDevice));
+  if ((s = groups_pack_tc(gr, 0))) return s;
+  CK(cudaDeviceSynchronize());
   *out = guard.release();
   return GPJC_OK;
 }
@@ -538,9 +610,22 @@ extern "C" gpjc_status gpjc_groups_roi(const gpjc_groups* gr, int32_t* h_pix) {
 extern "C" gpjc_status gpjc_compress(const gpjc_groups* gr, const float* d_S, float* d_Sc, gpjc_precision prec,
                                      void* stream) {
   if (!gr || !d_S || !d_Sc) return fail(GPJC_EINVAL, "null argument");
-  if (prec != GPJC_FP32) return fail(GPJC_EUNSUPPORTED, "this entry point handles FP32; see gpjc_compress_bf16");
   const Geo& g = gr->plan->geo;
-  CK(launch_compress_fp32(g, (const float2*)d_S, g.n_lines, gr->AT, (float2*)d_Sc, (cudaStream_t)stream));
+  if (prec == GPJC_FP32) {
+    CK(launch_compress_fp32(g, (const float2*)d_S, g.n_lines, gr->AT, (float2*)d_Sc, (cudaStream_t)stream));
+    return GPJC_OK;
+  }
+  if (prec != GPJC_BF16 && prec != GPJC_FP16) return fail(GPJC_EINVAL, "unknown precision");
+  const gpjc_plan* p = gr->plan;
+  if (!p->tc_ok) return fail(GPJC_EUNSUPPORTED, "tensor-core compression needs a periodic group map");
+  if (((uintptr_t)d_S) & 15) return fail(GPJC_EINVAL, "d_S must be 16-byte aligned");
+  TcGeom t = p->tc32;
+  t.scale = gr->scale;
+  CUtensorMap map;
+  if (!make_tc_tmap(t, d_S, g.n_lines, 4, &map)) return fail(GPJC_ECUDA, "cuTensorMapEncodeTiled failed");
+  const int fmt = prec == GPJC_BF16 ? 1 : 0;
+  CK(launch_tc_compress(map, t, fmt, 4, gr->tc_bc[fmt], (float2*)d_Sc, g.n_lines, gr->tc_status,
+                        (cudaStream_t)stream));
   return GPJC_OK;
 }
 
@@ -557,6 +642,8 @@ struct gpjc_op {
   float2 *Hpart, *T, *H2, *xparts;
   float2 *vb, *vr, *vp, *vy, *vv, *vtmp;
   float2 *V, *TV;  // lazily allocated (simulation)
+  void* V16;       // 16-bit hybrid data [rows][nc][ntx] of the tensor-core operator
+  CUtensorMap map16;
   double* partials;
   int npartials;
   unsigned* counter;
@@ -608,9 +695,10 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
                                       int32_t nchunk, gpjc_op** out) {
   if (!gr || !d_coil || !out) return fail(GPJC_EINVAL, "null argument");
   *out = nullptr;
-  if (prec != GPJC_FP32 && prec != GPJC_BF16) return fail(GPJC_EINVAL, "unknown precision");
-  if (prec == GPJC_BF16) return fail(GPJC_EUNSUPPORTED, "BF16 operator not built in this version");
+  if (prec != GPJC_FP32 && prec != GPJC_BF16 && prec != GPJC_FP16) return fail(GPJC_EINVAL, "unknown precision");
   const gpjc_plan* p = gr->plan;
+  if (prec != GPJC_FP32 && !p->tc_ok)
+    return fail(GPJC_EUNSUPPORTED, "the tensor-core operator needs a periodic group map");
   if (nchunk < 0 || nchunk > p->nc) return fail(GPJC_EINVAL, "nchunk must be in [0, nc]");
   auto* op = new (std::nothrow) gpjc_op();
   if (!op) return fail(GPJC_ENOMEM, "host allocation");
@@ -651,6 +739,14 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   CK(cudaMemset(op->sc, 0, SC_N * sizeof(double)));
   CK(cudaMemset(op->status, 0, 4 * sizeof(int)));
   op->V = op->TV = nullptr;
+  op->V16 = nullptr;
+  if (prec != GPJC_FP32) {
+    uint32_t* v16;
+    if ((s = m.alloc(&v16, (size_t)g.rows * g.nc * g.ntx))) return s;
+    op->V16 = v16;
+    if (!make_tc_tmap(p->tc16, op->V16, g.rows, 2, &op->map16))
+      return fail(GPJC_ECUDA, "cuTensorMapEncodeTiled failed");
+  }
   op->gexec = nullptr;
   op->graph_kernels = 0;
   {
@@ -682,9 +778,19 @@ extern "C" void gpjc_op_destroy(gpjc_op* op) {
 }
 
 // --- internal launch sequences (no validation) ---
-// readout stage of E_c into op->Hpart (register-tiled kernel when the plan has tiles)
+// readout stage of E_c into op->Hpart (register-tiled kernel when the plan has
+// tiles; 16-bit hybrid data + tensor-core compression for BF16 / FP16)
 static cudaError_t readout_fwd(const gpjc_op* op, const float2* x, cudaStream_t st) {
   const gpjc_plan* p = op->plan;
+  if (op->prec != GPJC_FP32) {
+    const int fmt = op->prec == GPJC_BF16 ? 1 : 0;
+    cudaError_t e = fmt ? launch_sim_fwd_bf16(p->geo, x, op->coil, op->V16, op->nchunk, st)
+                        : launch_sim_fwd_f16(p->geo, x, op->coil, op->V16, op->nchunk, st);
+    if (e != cudaSuccess) return e;
+    TcGeom t = p->tc16;
+    t.scale = op->gr->scale;
+    return launch_tc_compress(op->map16, t, fmt, 2, op->gr->tc_bc[fmt], op->Hpart, p->geo.rows, op->status, st);
+  }
   if (p->rt_f.rb && !op->legacy_readout)
     return launch_k1f_tiled(p->geo, p->rt_f, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st);
   return launch_k1_fwd_fp32(p->geo, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st);
@@ -692,6 +798,15 @@ static cudaError_t readout_fwd(const gpjc_op* op, const float2* x, cudaStream_t 
 // readout stage of E_c^H from op->H2 into op->xparts
 static cudaError_t readout_adj(const gpjc_op* op, cudaStream_t st) {
   const gpjc_plan* p = op->plan;
+  if (op->prec != GPJC_FP32) {
+    const int fmt = op->prec == GPJC_BF16 ? 1 : 0;
+    TcGeom t = p->tc16;
+    t.scale = op->gr->scale;
+    cudaError_t e = launch_tc_expand(t, fmt, op->H2, op->gr->tc_bx[fmt], op->V16, p->geo.rows, op->status, st);
+    if (e != cudaSuccess) return e;
+    return fmt ? launch_sim_adj_bf16(p->geo, op->V16, op->coil, op->xparts, op->nchunk, st)
+               : launch_sim_adj_f16(p->geo, op->V16, op->coil, op->xparts, op->nchunk, st);
+  }
   if (p->rt_a.rb && !op->legacy_readout)
     return launch_k1a_tiled(p->geo, p->rt_a, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st);
   return launch_k1_adj_fp32(p->geo, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st);
@@ -705,7 +820,7 @@ static gpjc_status op_fwd(const gpjc_op* cop, const float2* x, float2* y, cudaSt
   CK(readout_fwd(op, x, st));
   prof_end(op, st, m);
   prof_begin(op, GPJC_STAGE_PHASE_ENCODE, st, &m);
-  CK(launch_pe_fwd(g, op->Hpart, op->nchunk, g.ntxc, op->T, y, st));
+  CK(launch_pe_fwd(g, op->Hpart, op->prec == GPJC_FP32 ? op->nchunk : 1, g.ntxc, op->T, y, st));
   prof_end(op, st, m);
   return GPJC_OK;
 }
@@ -732,7 +847,8 @@ static gpjc_status op_normal_parts(const gpjc_op* cop, const float2* x, double* 
   CK(readout_fwd(op, x, st));
   prof_end(op, st, m);
   prof_begin(op, GPJC_STAGE_PHASE_ENCODE, st, &m);
-  CK(launch_pe_normal(g, op->Hpart, op->nchunk, g.ntxc, op->T, op->H2, op->partials, op->counter, qq, st));
+  CK(launch_pe_normal(g, op->Hpart, op->prec == GPJC_FP32 ? op->nchunk : 1, g.ntxc, op->T, op->H2, op->partials,
+                      op->counter, qq, st));
   prof_end(op, st, m);
   prof_begin(op, GPJC_STAGE_READOUT_ADJ, st, &m);
   CK(readout_adj(op, st));

@@ -54,6 +54,24 @@ struct RTiles {
   const int4* cols;  // [nt * 4]
 };
 
+// Tensor-core group compression geometry (k_tc.cu).  The group map must be
+// periodic: patch p belongs to group p mod G and P = G w divides N_tx, so
+// group g's occurrences start at g w + q P (q < n_occ).
+struct TcGeom {
+  int G, w, nc, ns, ntx, ntxc;
+  int n_occ, P, lt;          // occurrences per readout line, period, lines per 128-column tile
+  int ncc, nchunks, Kc;      // coils per K chunk, chunks, K per chunk (multiple of 16)
+  int npad;                  // N of the compression GEMM: 2 keep_max rounded up to 16
+  int box0, xalign;          // TMA inner box (elements) and coordinate alignment
+  int stg_tx, stg_bytes;     // staging bytes per chunk (exact, allocated)
+  int tmem_cols;             // TMEM columns of the compression accumulator
+  int Kx, nexp;              // expansion GEMM: K = 2 keep_max rounded to 16, N = 2 N_s rounded to 16
+  const int* keep;
+  const int* aoff;
+  const int* poff;
+  const float* scale;
+};
+
 // Device status word values (written by kernels, read by the host).
 enum DevStatus : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2, kDevBadIndex = 3 };
 

@@ -1,5 +1,6 @@
 // Kernel launchers (host functions defined in the kernel translation units).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -48,6 +49,21 @@ cudaError_t launch_k1f_tiled(const Geo& g, const RTiles& tl, const float2* x, co
                              const float2* AT, float2* Hpart, int nchunk, cudaStream_t st);
 cudaError_t launch_k1a_tiled(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,
                              const float2* A, float2* xpart, int nchunk, cudaStream_t st);
+
+// ---- tensor-core compression (k_tc.cu)
+bool make_tc_tmap(const TcGeom& t, const void* base, int lines, int ebytes, CUtensorMap* map);
+size_t tc_compress_smem(const TcGeom& t);
+size_t tc_expand_smem(const TcGeom& t);
+cudaError_t launch_tc_pack(const TcGeom& t, int fmt, const float2* A, const float* scale, uint16_t* Bc,
+                           uint16_t* Bx, cudaStream_t st);
+cudaError_t launch_tc_compress(const CUtensorMap& map, const TcGeom& t, int fmt, int src_bytes, const uint16_t* Bc,
+                               float2* out, int lines, int* status, cudaStream_t st);
+cudaError_t launch_tc_expand(const TcGeom& t, int fmt, const float2* H, const uint16_t* Bx, void* V, int rows,
+                             int* status, cudaStream_t st);
+cudaError_t launch_sim_fwd_f16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
+                               cudaStream_t st);
+cudaError_t launch_sim_adj_f16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,
+                               cudaStream_t st);
 
 // ---- groups (k_groups.cu)
 cudaError_t launch_roi_count(const Geo& g, const float2* coil, const uint8_t* roi, int* blockcount, int nblk,

@@ -17,6 +17,7 @@
 // sampled lines, and for E_c^H E_c the fused mask-projection with the
 // squared norm ||E_c p||^2 accumulated for CG.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "gpjc_device.cuh"
 #include "gpjc_kernels.h"
@@ -207,8 +208,16 @@ template <>
 __device__ __forceinline__ void store_v<__nv_bfloat162>(__nv_bfloat162* p, float2 v) {
   *p = __floats2bfloat162_rn(v.x, v.y);
 }
+template <>
+__device__ __forceinline__ void store_v<__half2>(__half2* p, float2 v) {
+  *p = __floats2half2_rn(v.x, v.y);
+}
 template <typename VT>
 __device__ __forceinline__ float2 load_v(const VT* p);
+template <>
+__device__ __forceinline__ float2 load_v<__half2>(const __half2* p) {
+  return __half22float2(*p);
+}
 template <>
 __device__ __forceinline__ float2 load_v<float2>(const float2* p) { return *p; }
 template <>
@@ -604,6 +613,14 @@ cudaError_t launch_sim_fwd(const Geo& g, const float2* x, const float2* coil, fl
 cudaError_t launch_sim_fwd_bf16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
                                 cudaStream_t st) {
   return launch_sim_fwd_t<__nv_bfloat162>(g, x, coil, (__nv_bfloat162*)V, nchunk, st);
+}
+cudaError_t launch_sim_fwd_f16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
+                               cudaStream_t st) {
+  return launch_sim_fwd_t<__half2>(g, x, coil, (__half2*)V, nchunk, st);
+}
+cudaError_t launch_sim_adj_f16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,
+                               cudaStream_t st) {
+  return launch_sim_adj_t<__half2>(g, (const __half2*)V, coil, xpart, nchunk, st);
 }
 cudaError_t launch_sim_adj(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
                            cudaStream_t st) {

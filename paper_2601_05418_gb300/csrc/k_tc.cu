@@ -1,0 +1,518 @@
+// Tensor-core (tcgen05) group compression and its adjoint, 16-bit operands
+// (BF16 or FP16) with FP32 accumulation in tensor memory (Eq. 13-15).
+//
+// Complex products are embedded in real GEMMs with the contraction index
+// interleaved as (sample i, re/im) -- the natural memory order of complex
+// data -- and the output index interleaved as (k, re/im):
+//   D[col][2k + c'] = sum_{i,c} X[col][2i + c] B[2i + c][2k + c'],
+// B = [[Re A, Im A], [-Im A, Re A]] per (i, k).  For the compression
+// (S' = A_g s, Eq. 13) a block owns 128 columns (lines x occurrences of
+// group g); the patch samples of a chunk of coils are staged by one 4D TMA
+// copy per chunk (periodic view [line][coil][occurrence][period]),
+// converted to the no-swizzle K-major core-matrix layout, and one thread
+// issues the MMAs (M = 128, N = 2 keep rounded to 16, K = 16 per
+// instruction) into a TMEM accumulator that the four warps read back.
+// B is pre-packed in global memory in the exact shared-memory image and
+// copied with one bulk copy per chunk.  A per-group scale maps A_g to
+// [-1, 1] before rounding and is re-applied in the epilogue.
+//
+// The adjoint (A_g^H applied to the compressed columns) is the same GEMM
+// with the roles of k and i exchanged and N tiled by 256.
+//
+// Every wait on an mbarrier is bounded; on timeout the block records
+// kDevTimeout in the status word, drains what it issued (again bounded),
+// frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include "gpjc_device.cuh"
+#include "gpjc_kernels.h"
+
+namespace gpjc {
+
+constexpr int kTcThreads = 128;
+// a wait gives up after about half a second of SM clock cycles
+constexpr long long kWaitCycles = 1000000000ll;
+
+// ------------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    if (clock64() - t0 > kWaitCycles) return false;
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+      "l"((unsigned long long)map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"((unsigned long long)src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// Shared-memory matrix descriptor: no swizzle, K-major core matrices of
+// 8 rows x 16 bytes; lbo = byte step between core matrices along K, sbo =
+// byte step between 8-row groups.
+__device__ __forceinline__ uint64_t umma_desc(const void* p, uint32_t lbo, uint32_t sbo) {
+  const uint64_t a = (uint64_t)(smem_u32(p) & 0x3FFFF) >> 4;
+  return a | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) | ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) |
+         ((uint64_t)1 << 46);
+}
+// Instruction descriptor of kind::f16: FP32 accumulate, A/B both FP16
+// (fmt 0) or both BF16 (fmt 1), both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_f16(int fmt, int n) {
+  return (1u << 4) | ((uint32_t)fmt << 7) | ((uint32_t)fmt << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 16-bit element conversions
+template <int FMT>
+__device__ __forceinline__ uint32_t pack2(float a, float b);
+template <>
+__device__ __forceinline__ uint32_t pack2<1>(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+template <>
+__device__ __forceinline__ uint32_t pack2<0>(float a, float b) {
+  __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+template <int FMT>
+__device__ __forceinline__ float2 unpack2(uint32_t v);
+template <>
+__device__ __forceinline__ float2 unpack2<1>(uint32_t v) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
+  return __bfloat1622float2(h);
+}
+template <>
+__device__ __forceinline__ float2 unpack2<0>(uint32_t v) {
+  __half2 h = *reinterpret_cast<__half2*>(&v);
+  return __half22float2(h);
+}
+
+// element offset of (row, k) in a no-swizzle K-major core-matrix image with
+// Kt columns (Kt multiple of 8)
+__host__ __device__ __forceinline__ int core_off(int row, int k, int Kt) {
+  return (row >> 3) * (Kt << 3) + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
+}
+
+// ------------------------------------------------------------------ packing --
+// Compression B per (group, coil chunk): rows 2k + c' (N), columns
+// 2 (n_local w + tau) + c (K), core-matrix image, values of A_g / scale_g.
+template <int FMT>
+__global__ void k_tc_pack_comp(TcGeom t, const float2* __restrict__ A, const float* __restrict__ scale,
+                               uint16_t* __restrict__ B) {
+  const int g = blockIdx.y, chunk = blockIdx.z;
+  const size_t per = (size_t)t.npad * t.Kc;
+  uint16_t* Bg = B + ((size_t)g * t.nchunks + chunk) * per;
+  const float inv = scale[g] > 0.f ? 1.0f / scale[g] : 0.f;
+  const int keep = t.keep[g];
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < t.npad * t.Kc; idx += gridDim.x * blockDim.x) {
+    const int nr = idx / t.Kc, kk = idx - nr * t.Kc;
+    const int kout = nr >> 1, cout = nr & 1;
+    const int nl = kk / (2 * t.w), rem = kk - nl * 2 * t.w;
+    const int tau = rem >> 1, cin = rem & 1;
+    const int n = chunk * t.ncc + nl;
+    float v = 0.f;
+    if (kout < keep && n < t.nc && nl < t.ncc) {
+      const float2 a = A[t.aoff[g] + (size_t)kout * t.ns + n * t.w + tau];
+      const float re = a.x * inv, im = a.y * inv;
+      v = (cin == 0) ? (cout == 0 ? re : im) : (cout == 0 ? -im : re);
+    }
+    const uint32_t p = pack2<FMT>(v, 0.f);
+    Bg[core_off(nr, kk, t.Kc)] = (uint16_t)(p & 0xFFFF);
+  }
+}
+
+// Expansion B per (group, N tile of 256): rows 2 i + c (N, i = n w + tau),
+// columns 2 k + c' (K, padded to Kx), values of conj(A_g)^T / scale_g:
+//   U_i = sum_k conj(A_ki) h_k  ->  [Re U; Im U] from [Re h; Im h].
+template <int FMT>
+__global__ void k_tc_pack_exp(TcGeom t, const float2* __restrict__ A, const float* __restrict__ scale,
+                              uint16_t* __restrict__ B) {
+  const int g = blockIdx.y;
+  const size_t per = (size_t)t.nexp * t.Kx;
+  uint16_t* Bg = B + (size_t)g * per;
+  const float inv = scale[g] > 0.f ? 1.0f / scale[g] : 0.f;
+  const int keep = t.keep[g];
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < t.nexp * t.Kx; idx += gridDim.x * blockDim.x) {
+    const int nr = idx / t.Kx, kk = idx - nr * t.Kx;
+    const int i = nr >> 1, c = nr & 1;      // output sample and re/im
+    const int k = kk >> 1, cp = kk & 1;      // input kept component and re/im
+    float v = 0.f;
+    if (i < t.ns && k < keep) {
+      const float2 a = A[t.aoff[g] + (size_t)k * t.ns + i];
+      const float re = a.x * inv, im = a.y * inv;
+      // Re U = Re A Re h + Im A Im h ; Im U = Re A Im h - Im A Re h
+      v = (c == 0) ? (cp == 0 ? re : im) : (cp == 0 ? -im : re);
+    }
+    // N tiles of 256 rows are stored one after another, each its own image
+    const int tile = nr >> 8, rr = nr & 255;
+    Bg[(size_t)tile * 256 * t.Kx + core_off(rr, kk, t.Kx)] = (uint16_t)(pack2<FMT>(v, 0.f) & 0xFFFF);
+  }
+}
+
+// ------------------------------------------------------------------ compression GEMM --
+// Source element: float (SRC_BYTES = 4, converted) or the 16-bit operand
+// type itself (SRC_BYTES = 2).  Output: out[line][off_p + k] complex64.
+template <int FMT, int SRC_BYTES>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_constant__ CUtensorMap tmap, TcGeom t,
+                                                              const uint16_t* __restrict__ Bpk,
+                                                              float2* __restrict__ out, int n_lines,
+                                                              int* status) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  const int g = blockIdx.y;
+  const int l0 = blockIdx.x * t.lt;
+  unsigned char* stg = tsm;                                   // staging [lt][ncc][n_occ][box0]
+  uint16_t* At = (uint16_t*)(tsm + t.stg_bytes);              // 128 x Kc core image
+  uint16_t* Bt = At + 128 * t.Kc;                             // npad x Kc core image
+  uint64_t* bars = (uint64_t*)(Bt + (size_t)t.npad * t.Kc);   // [0] load, [1] mma
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, t.tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = idesc_f16(FMT, t.npad);
+  const int x0 = ((2 * g * t.w) / t.xalign) * t.xalign;
+  const int shift = 2 * g * t.w - x0;
+  const uint32_t bbytes = (uint32_t)(t.npad * t.Kc * 2);
+  uint32_t ph_ld = 0, ph_mma = 0;
+  bool ok = true;
+  const int m = tid;  // A row = output column (line l, occurrence q)
+  const int l = m / t.n_occ, q = m - l * t.n_occ;
+  for (int c = 0; c < t.nchunks && ok; ++c) {
+    if (tid == 0) {
+      mbar_expect_tx(&bars[0], (uint32_t)t.stg_tx + bbytes);
+      tma_load_4d(stg, &tmap, x0, 0, c * t.ncc, l0, &bars[0]);
+      bulk_g2s(Bt, Bpk + ((size_t)g * t.nchunks + c) * t.npad * t.Kc, bbytes, &bars[0]);
+    }
+    ok = mbar_wait(&bars[0], ph_ld);
+    ph_ld ^= 1;
+    if (!ok) break;
+    // staging -> 16-bit core image (row m holds its column's samples of the chunk)
+    for (int nl = 0; nl < t.ncc; ++nl) {
+      const size_t base = ((size_t)(l * t.ncc + nl) * t.n_occ + q) * t.box0 + shift;
+      for (int tau = 0; tau < t.w; ++tau) {
+        uint32_t pk;
+        if (SRC_BYTES == 4) {
+          const float* s = (const float*)stg + base + 2 * tau;
+          pk = pack2<FMT>(s[0], s[1]);
+        } else {
+          const uint16_t* s = (const uint16_t*)stg + base + 2 * tau;
+          pk = (uint32_t)s[0] | ((uint32_t)s[1] << 16);
+        }
+        const int k = 2 * (nl * t.w + tau);
+        *(uint32_t*)(At + core_off(m, k, t.Kc)) = pk;
+      }
+    }
+    for (int k = 2 * t.ncc * t.w; k < t.Kc; k += 2) *(uint32_t*)(At + core_off(m, k, t.Kc)) = 0u;
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t sbo = (uint32_t)(t.Kc / 8) * 128;
+      for (int ks = 0; ks < t.Kc / 16; ++ks) {
+        const uint64_t ad = umma_desc(At + ks * 16 * 8, 128, sbo);
+        const uint64_t bd = umma_desc(Bt + ks * 16 * 8, 128, sbo);
+        mma_f16(tmem, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+      }
+      mma_commit(&bars[1]);
+    }
+    ok = mbar_wait(&bars[1], ph_mma);
+    ph_mma ^= 1;
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(status, (int)kDevTimeout);
+    // drain whatever is still in flight before releasing the memory
+    mbar_wait(&bars[0], ph_ld);
+    mbar_wait(&bars[1], ph_mma);
+  } else {
+    tc_fence_after();
+    // epilogue: lane m of TMEM holds column m; 8 fp32 columns = 4 complex values per load
+    const int line = l0 + l;
+    const int p = (g * t.w + q * t.P) / t.w;
+    const bool valid = line < n_lines;
+    const float s = t.scale[g];
+    const int keep = t.keep[g];
+    float2* o = out + (size_t)line * t.ntxc + (valid ? t.poff[p] : 0);
+    for (int col = 0; col < t.npad; col += 8) {
+      float v[8];
+      tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = col / 2 + j;
+          if (k < keep) o[k] = make_float2(v[2 * j] * s, v[2 * j + 1] * s);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, t.tmem_cols);
+}
+
+// ------------------------------------------------------------------ expansion GEMM --
+// V[row][n][p w + tau] = sum_k conj(A_g[k][n w + tau]) H[row][off_p + k]
+// (16-bit output).  A block owns 128 columns (rows x occurrences of g).
+template <int FMT>
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const float2* __restrict__ H,
+                                                            const uint16_t* __restrict__ Bpk,
+                                                            uint32_t* __restrict__ V, int n_rows, int* status) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  const int g = blockIdx.y;
+  const int r0 = blockIdx.x * t.lt;
+  uint16_t* At = (uint16_t*)tsm;                        // 128 x Kx
+  uint16_t* Bt = At + 128 * t.Kx;                       // 256 x Kx
+  uint64_t* bars = (uint64_t*)(Bt + 256 * t.Kx);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, 256);
+  const int m = tid;
+  const int l = m / t.n_occ, q = m - l * t.n_occ;
+  const int row = r0 + l;
+  const int p = (g * t.w + q * t.P) / t.w;
+  const bool valid = row < n_rows;
+  const int keep = t.keep[g];
+  // A operand: this column's kept components (FP32 -> 16 bit)
+  const float2* h = H + (size_t)(valid ? row : 0) * t.ntxc + t.poff[p];
+  for (int k = 0; k < t.Kx / 2; ++k) {
+    const float2 v = (valid && k < keep) ? h[k] : make_float2(0.f, 0.f);
+    *(uint32_t*)(At + core_off(m, 2 * k, t.Kx)) = pack2<FMT>(v.x, v.y);
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const float s = t.scale[g];
+  uint32_t ph_ld = 0, ph_mma = 0;
+  bool ok = true;
+  const int ntiles = (t.nexp + 255) / 256;
+  for (int nt = 0; nt < ntiles && ok; ++nt) {
+    const int nrows = min(256, t.nexp - nt * 256);  // multiple of 16
+    const uint32_t bbytes = (uint32_t)(nrows * t.Kx * 2);
+    if (tid == 0) {
+      mbar_expect_tx(&bars[0], bbytes);
+      bulk_g2s(Bt, Bpk + (size_t)g * t.nexp * t.Kx + (size_t)nt * 256 * t.Kx, bbytes, &bars[0]);
+    }
+    ok = mbar_wait(&bars[0], ph_ld);
+    ph_ld ^= 1;
+    if (!ok) break;
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t sbo = (uint32_t)(t.Kx / 8) * 128;
+      const uint32_t idesc = idesc_f16(FMT, nrows);
+      for (int ks = 0; ks < t.Kx / 16; ++ks) {
+        const uint64_t ad = umma_desc(At + ks * 16 * 8, 128, sbo);
+        const uint64_t bd = umma_desc(Bt + ks * 16 * 8, 128, sbo);
+        mma_f16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+      }
+      mma_commit(&bars[1]);
+    }
+    ok = mbar_wait(&bars[1], ph_mma);
+    ph_mma ^= 1;
+    if (!ok) break;
+    tc_fence_after();
+    for (int col = 0; col < nrows; col += 8) {
+      float v[8];
+      tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int i = (nt * 256 + col) / 2 + j;  // patch vector index n w + tau
+          if (i < t.ns) {
+            const int n = i / t.w, tau = i - n * t.w;
+            V[((size_t)row * t.nc + n) * t.ntx + p * t.w + tau] = pack2<FMT>(v[2 * j] * s, v[2 * j + 1] * s);
+          }
+        }
+      }
+    }
+    // all lanes must finish reading TMEM before the next tile's MMAs overwrite it
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(status, (int)kDevTimeout);
+    mbar_wait(&bars[0], ph_ld);
+    mbar_wait(&bars[1], ph_mma);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// ------------------------------------------------------------------ host side --
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// 4D periodic view of [lines][nc][ntx] complex data with elements of
+// `ebytes` (4 = float, 2 = 16-bit): dims (2P, n_occ, nc, lines).
+bool make_tc_tmap(const TcGeom& t, const void* base, int lines, int ebytes, CUtensorMap* map) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  const cuuint64_t dims[4] = {(cuuint64_t)(2 * t.P), (cuuint64_t)t.n_occ, (cuuint64_t)t.nc, (cuuint64_t)lines};
+  const cuuint64_t strides[3] = {(cuuint64_t)(2 * t.P) * ebytes, (cuuint64_t)(2 * t.ntx) * ebytes,
+                                 (cuuint64_t)t.nc * 2 * t.ntx * ebytes};
+  const cuuint32_t box[4] = {(cuuint32_t)t.box0, (cuuint32_t)t.n_occ, (cuuint32_t)t.ncc, (cuuint32_t)t.lt};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUresult r = enc(map, ebytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 4,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+size_t tc_compress_smem(const TcGeom& t) {
+  return (size_t)t.stg_bytes + (size_t)128 * t.Kc * 2 + (size_t)t.npad * t.Kc * 2 + 64;
+}
+size_t tc_expand_smem(const TcGeom& t) { return (size_t)128 * t.Kx * 2 + (size_t)256 * t.Kx * 2 + 64; }
+
+cudaError_t launch_tc_pack(const TcGeom& t, int fmt, const float2* A, const float* scale, uint16_t* Bc,
+                           uint16_t* Bx, cudaStream_t st) {
+  dim3 gc(8, t.G, t.nchunks), gx(8, t.G);
+  if (fmt == 1) {
+    note_launches(1); k_tc_pack_comp<1><<<gc, 256, 0, st>>>(t, A, scale, Bc);
+    note_launches(1); k_tc_pack_exp<1><<<gx, 256, 0, st>>>(t, A, scale, Bx);
+  } else {
+    note_launches(1); k_tc_pack_comp<0><<<gc, 256, 0, st>>>(t, A, scale, Bc);
+    note_launches(1); k_tc_pack_exp<0><<<gx, 256, 0, st>>>(t, A, scale, Bx);
+  }
+  return cudaGetLastError();
+}
+
+template <int FMT, int SB>
+static cudaError_t launch_comp_t(const CUtensorMap& map, const TcGeom& t, const uint16_t* Bc, float2* out,
+                                 int lines, int* status, cudaStream_t st) {
+  const size_t sm = tc_compress_smem(t);
+  static size_t attr = 0;
+  if (sm > attr) {
+    cudaFuncSetAttribute(k_tc_compress<FMT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = sm;
+  }
+  dim3 grid((lines + t.lt - 1) / t.lt, t.G);
+  note_launches(1); k_tc_compress<FMT, SB><<<grid, kTcThreads, sm, st>>>(map, t, Bc, out, lines, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_compress(const CUtensorMap& map, const TcGeom& t, int fmt, int src_bytes, const uint16_t* Bc,
+                               float2* out, int lines, int* status, cudaStream_t st) {
+  if (fmt == 1 && src_bytes == 4) return launch_comp_t<1, 4>(map, t, Bc, out, lines, status, st);
+  if (fmt == 1 && src_bytes == 2) return launch_comp_t<1, 2>(map, t, Bc, out, lines, status, st);
+  if (fmt == 0 && src_bytes == 4) return launch_comp_t<0, 4>(map, t, Bc, out, lines, status, st);
+  if (fmt == 0 && src_bytes == 2) return launch_comp_t<0, 2>(map, t, Bc, out, lines, status, st);
+  return cudaErrorInvalidValue;
+}
+
+template <int FMT>
+static cudaError_t launch_exp_t(const TcGeom& t, const float2* H, const uint16_t* Bx, void* V, int rows,
+                                int* status, cudaStream_t st) {
+  const size_t sm = tc_expand_smem(t);
+  static size_t attr = 0;
+  if (sm > attr) {
+    cudaFuncSetAttribute(k_tc_expand<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = sm;
+  }
+  dim3 grid((rows + t.lt - 1) / t.lt, t.G);
+  note_launches(1); k_tc_expand<FMT><<<grid, kTcThreads, sm, st>>>(t, H, Bx, (uint32_t*)V, rows, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_expand(const TcGeom& t, int fmt, const float2* H, const uint16_t* Bx, void* V, int rows,
+                             int* status, cudaStream_t st) {
+  return fmt == 1 ? launch_exp_t<1>(t, H, Bx, V, rows, status, st) : launch_exp_t<0>(t, H, Bx, V, rows, status, st);
+}
+
+}  // namespace gpjc

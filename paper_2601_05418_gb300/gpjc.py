@@ -22,7 +22,7 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 GPJC_OK, GPJC_EINVAL, GPJC_ENOMEM, GPJC_ECUDA, GPJC_ETIMEOUT, GPJC_ENONFINITE, GPJC_EUNSUPPORTED = range(7)
-FP32, BF16 = 0, 1
+FP32, BF16, FP16 = 0, 1, 2
 CG, FISTA = 0, 1
 _P = C.c_void_p
 _I32P = C.POINTER(C.c_int32)

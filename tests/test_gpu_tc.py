@@ -1,0 +1,129 @@
+"""Tensor-core (tcgen05) compression and operator: BF16 / FP16 operands,
+FP32 accumulation, against the FP64 oracle.
+
+Tolerances: a 16-bit operand carries a relative rounding error of 2^-9
+(BF16) or 2^-12 (FP16); a contraction over N_s terms with random phases
+keeps the relative error of each output at that order, so single
+applications are held to a relative L2 error of 1e-2 (BF16) / 2e-3 (FP16),
+and reconstructed images to NRMSE 1e-3 (the reduced-precision bar).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2601_05418_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def gp():
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_05418_gb300 import gpjc
+
+    return gpjc
+
+
+def to_dev(a, dtype=np.complex64):
+    return torch.from_numpy(np.ascontiguousarray(a.astype(dtype))).to(DEV)
+
+
+def to_np(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+TOL = {1: 1e-2, 2: 2e-3}  # BF16, FP16
+
+
+def geoms():
+    return {"2d128": synth.workload("2d128").geom, "3d56": synth.workload("3d56").geom,
+            "2d64": synth._geom_2d(64, 8, 4, 8, 2.5, 16, 8.0, 3)}
+
+
+def case(g, seed):
+    coils = synth.coil_maps(g.nx, g.ny, g.nz, g.nc, seed)
+    rho = synth.phantom(g.nx, g.ny, g.nz)
+    return coils, rho, synth.roi_mask(rho)
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("name", ["2d128", "3d56"])
+def test_tc_compress_matches_oracle(gp, name, prec):
+    g = geoms()[name]
+    coils, rho, roi = case(g, 41)
+    As, _, _ = O.build_groups(g, coils, roi)
+    S = synth.complex_normal((g.n_lines, g.nc, g.ntx), 42)
+    grp = gp.Groups.from_matrices(gp.Plan(g), As)
+    Sc = to_np(gp.compress(grp, to_dev(S), prec))
+    assert rel(Sc, O.compress(g, As, S)) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("name", ["2d128", "3d56"])
+def test_tc_operator_matches_oracle(gp, name, prec):
+    g = geoms()[name]
+    coils, rho, roi = case(g, 43)
+    As, _, _ = O.build_groups(g, coils, roi)
+    op = gp.Operator(gp.Groups.from_matrices(gp.Plan(g), As), to_dev(coils), prec)
+    x = synth.complex_normal(g.shape, 44)
+    y = to_np(op.E(to_dev(x)))
+    y_ref = O.Ec_apply(g, coils, As, x)
+    assert rel(y, y_ref) < TOL[prec]
+    v = synth.complex_normal(y_ref.shape, 45)
+    xa = to_np(op.EH(to_dev(v)))
+    assert rel(xa, O.EcH_apply(g, coils, As, v)) < TOL[prec]
+
+
+def test_tc_unsupported_group_map_is_rejected(gp):
+    g = synth.tiny_geometry(nx=40, ny=36, nz=1, nc=5, os=3, cycles=4.0, kappa_y=1.7, n_groups=3,
+                            lines="regular", r=2)
+    coils, rho, roi = case(g, 46)
+    As, _, _ = O.build_groups(g, coils, roi)
+    grp = gp.Groups.from_matrices(gp.Plan(g), As)
+    with pytest.raises(gp.GpjcError) as ei:
+        gp.Operator(grp, to_dev(coils), gp.BF16)
+    assert ei.value.status == gp.GPJC_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tc_cg_image_within_1e3(gp, prec):
+    wl = synth.workload("2d128")
+    g = wl.geom
+    c = synth.make_case(wl)
+    S = O.simulate(g, c.coils, c.rho, c.noise)
+    As, _, _ = O.build_groups(g, c.coils, c.roi)
+    x_ref, _ = O.reconstruct(g, c.coils, As, O.compress(g, As, S), "cg", wl.iters)
+    plan = gp.Plan(g)
+    c_d = to_dev(c.coils)
+    grp = gp.Groups.build(plan, c_d, to_dev(c.roi, np.uint8))
+    op = gp.Operator(grp, c_d, prec)
+    x, info = op.recon(gp.compress(grp, to_dev(S), prec), alg=gp.CG, iters=wl.iters)
+    assert info["status"] == 0
+    err = O.nrmse(to_np(x), x_ref)
+    assert err < 1e-3, err
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_tc_fista_image_within_1e3(gp, prec):
+    g = geoms()["2d64"]
+    coils, rho, roi = case(g, 47)
+    S = O.simulate(g, coils, rho, synth.complex_normal((g.n_lines, g.nc, g.ntx), 48, 1e-3))
+    As, _, _ = O.build_groups(g, coils, roi)
+    Sc = O.compress(g, As, S)
+    pb = O.Problem(g, coils, As)
+    b = pb.EcH(Sc)
+    L = O.power_lipschitz(pb.normal_c, b, 20)
+    x_ref = O.fista(pb.normal_c, b, L, 1e-3, 3, 30)
+    op = gp.Operator(gp.Groups.from_matrices(gp.Plan(g), As), to_dev(coils), prec)
+    x, _ = op.recon(gp.compress(op.groups, to_dev(S), prec), alg=gp.FISTA, iters=30, lam=1e-3, lipschitz=L,
+                    haar_levels=3)
+    err = O.nrmse(to_np(x), x_ref)
+    assert err < 1e-3, err
