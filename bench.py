@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpjc", choices=["gpjc", "reference"])
-    ap.add_argument("--workload", default="2d256", choices=["2d256", "2d256bf", "2d128"])
+    ap.add_argument("--workload", default="2d256", choices=["2d256", "2d256h", "2d256bf", "2d128"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -143,7 +143,7 @@ def run_gpjc(args, rank, world, local):
     wl = synth.workload(args.workload)
     g = wl.geom
     case = synth.make_case(wl)
-    prec = gpjc.BF16 if wl.precision == "bf16" else gpjc.FP32
+    prec = {"fp32": gpjc.FP32, "bf16": gpjc.BF16, "fp16": gpjc.FP16}[wl.precision]
     plan = gpjc.Plan(g)
     coils_h = torch.from_numpy(case.coils.astype(np.complex64)).pin_memory()
     roi_h = torch.from_numpy(case.roi).pin_memory()
@@ -265,7 +265,7 @@ def run_gpjc(args, rank, world, local):
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec == gpjc.BF16 else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": {gpjc.FP32: "f32", gpjc.BF16: "bf16", gpjc.FP16: "f16"}[prec],
         "data": "synthetic (seeded phantom, Gaussian-phase coils, regular R=3 mask, sigma 1e-3 noise)",
         "config": {"workload": wl.name, "matrix": [g.nz, g.ny, g.nx], "coils": g.nc, "os": g.os,
                    "groups": g.n_groups, "w": g.w, "keep": int(g.keep[0]), "ntx_c": plan.ntx_c,

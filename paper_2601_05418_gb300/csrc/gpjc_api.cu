@@ -741,7 +741,8 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   op->V = op->TV = nullptr;
   op->V16 = nullptr;
   if (prec != GPJC_FP32) {
-    uint32_t* v16;
+    // one buffer serves the 16-bit forward spectra and the FP32 adjoint spectra
+    float2* v16;
     if ((s = m.alloc(&v16, (size_t)g.rows * g.nc * g.ntx))) return s;
     op->V16 = v16;
     if (!make_tc_tmap(p->tc16, op->V16, g.rows, 2, &op->map16))
@@ -802,10 +803,10 @@ static cudaError_t readout_adj(const gpjc_op* op, cudaStream_t st) {
     const int fmt = op->prec == GPJC_BF16 ? 1 : 0;
     TcGeom t = p->tc16;
     t.scale = op->gr->scale;
-    cudaError_t e = launch_tc_expand(t, fmt, op->H2, op->gr->tc_bx[fmt], op->V16, p->geo.rows, op->status, st);
+    cudaError_t e =
+        launch_tc_expand(t, fmt, op->H2, op->gr->tc_bx[fmt], (float2*)op->V16, p->geo.rows, op->status, st);
     if (e != cudaSuccess) return e;
-    return fmt ? launch_sim_adj_bf16(p->geo, op->V16, op->coil, op->xparts, op->nchunk, st)
-               : launch_sim_adj_f16(p->geo, op->V16, op->coil, op->xparts, op->nchunk, st);
+    return launch_sim_adj(p->geo, (const float2*)op->V16, op->coil, op->xparts, op->nchunk, st);
   }
   if (p->rt_a.rb && !op->legacy_readout)
     return launch_k1a_tiled(p->geo, p->rt_a, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st);

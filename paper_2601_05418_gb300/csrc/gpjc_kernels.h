@@ -58,7 +58,7 @@ cudaError_t launch_tc_pack(const TcGeom& t, int fmt, const float2* A, const floa
                            uint16_t* Bx, cudaStream_t st);
 cudaError_t launch_tc_compress(const CUtensorMap& map, const TcGeom& t, int fmt, int src_bytes, const uint16_t* Bc,
                                float2* out, int lines, int* status, cudaStream_t st);
-cudaError_t launch_tc_expand(const TcGeom& t, int fmt, const float2* H, const uint16_t* Bx, void* V, int rows,
+cudaError_t launch_tc_expand(const TcGeom& t, int fmt, const float2* H, const uint16_t* Bx, float2* V, int rows,
                              int* status, cudaStream_t st);
 cudaError_t launch_sim_fwd_f16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
                                cudaStream_t st);

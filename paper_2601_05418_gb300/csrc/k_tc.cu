@@ -329,17 +329,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
 }
 
 // ------------------------------------------------------------------ expansion GEMM --
-// V[row][n][p w + tau] = sum_k conj(A_g[k][n w + tau]) H[row][off_p + k]
-// (16-bit output).  A block owns 128 columns (rows x occurrences of g).
+// V[row][n][p w + tau] = sum_k conj(A_g[k][n w + tau]) H[row][off_p + k],
+// FP32 output.  A block owns 128 columns (rows x occurrences of g).  The
+// FP32 input column is split into a 16-bit head and a 16-bit remainder
+// (two MMAs into the same accumulator), so only A_g is rounded to 16 bits:
+// rounding the compressed hybrid data itself would break the adjoint
+// pairing that CG relies on far more than rounding the matrix does.
 template <int FMT>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const float2* __restrict__ H,
                                                             const uint16_t* __restrict__ Bpk,
-                                                            uint32_t* __restrict__ V, int n_rows, int* status) {
+                                                            float2* __restrict__ V, int n_rows, int* status) {
   extern __shared__ __align__(1024) unsigned char tsm[];
   const int g = blockIdx.y;
   const int r0 = blockIdx.x * t.lt;
-  uint16_t* At = (uint16_t*)tsm;                        // 128 x Kx
-  uint16_t* Bt = At + 128 * t.Kx;                       // 256 x Kx
+  uint16_t* Ah = (uint16_t*)tsm;                        // 128 x Kx head
+  uint16_t* Al = Ah + 128 * t.Kx;                       // 128 x Kx remainder
+  uint16_t* Bt = Al + 128 * t.Kx;                       // 256 x Kx
   uint64_t* bars = (uint64_t*)(Bt + 256 * t.Kx);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
@@ -355,11 +360,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
   const int p = (g * t.w + q * t.P) / t.w;
   const bool valid = row < n_rows;
   const int keep = t.keep[g];
-  // A operand: this column's kept components (FP32 -> 16 bit)
   const float2* h = H + (size_t)(valid ? row : 0) * t.ntxc + t.poff[p];
   for (int k = 0; k < t.Kx / 2; ++k) {
     const float2 v = (valid && k < keep) ? h[k] : make_float2(0.f, 0.f);
-    *(uint32_t*)(At + core_off(m, 2 * k, t.Kx)) = pack2<FMT>(v.x, v.y);
+    const uint32_t hi = pack2<FMT>(v.x, v.y);
+    const float2 hv = unpack2<FMT>(hi);
+    *(uint32_t*)(Ah + core_off(m, 2 * k, t.Kx)) = hi;
+    *(uint32_t*)(Al + core_off(m, 2 * k, t.Kx)) = pack2<FMT>(v.x - hv.x, v.y - hv.y);
   }
   fence_async_smem();
   tc_fence_before();
@@ -385,9 +392,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
       const uint32_t sbo = (uint32_t)(t.Kx / 8) * 128;
       const uint32_t idesc = idesc_f16(FMT, nrows);
       for (int ks = 0; ks < t.Kx / 16; ++ks) {
-        const uint64_t ad = umma_desc(At + ks * 16 * 8, 128, sbo);
         const uint64_t bd = umma_desc(Bt + ks * 16 * 8, 128, sbo);
-        mma_f16(tmem, ad, bd, idesc, ks > 0 ? 1u : 0u);
+        mma_f16(tmem, umma_desc(Ah + ks * 16 * 8, 128, sbo), bd, idesc, ks > 0 ? 1u : 0u);
+        mma_f16(tmem, umma_desc(Al + ks * 16 * 8, 128, sbo), bd, idesc, 1u);
       }
       mma_commit(&bars[1]);
     }
@@ -404,7 +411,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
           const int i = (nt * 256 + col) / 2 + j;  // patch vector index n w + tau
           if (i < t.ns) {
             const int n = i / t.w, tau = i - n * t.w;
-            V[((size_t)row * t.nc + n) * t.ntx + p * t.w + tau] = pack2<FMT>(v[2 * j] * s, v[2 * j + 1] * s);
+            V[((size_t)row * t.nc + n) * t.ntx + p * t.w + tau] = make_float2(v[2 * j] * s, v[2 * j + 1] * s);
           }
         }
       }
@@ -458,7 +465,7 @@ bool make_tc_tmap(const TcGeom& t, const void* base, int lines, int ebytes, CUte
 size_t tc_compress_smem(const TcGeom& t) {
   return (size_t)t.stg_bytes + (size_t)128 * t.Kc * 2 + (size_t)t.npad * t.Kc * 2 + 64;
 }
-size_t tc_expand_smem(const TcGeom& t) { return (size_t)128 * t.Kx * 2 + (size_t)256 * t.Kx * 2 + 64; }
+size_t tc_expand_smem(const TcGeom& t) { return (size_t)2 * 128 * t.Kx * 2 + (size_t)256 * t.Kx * 2 + 64; }
 
 cudaError_t launch_tc_pack(const TcGeom& t, int fmt, const float2* A, const float* scale, uint16_t* Bc,
                            uint16_t* Bx, cudaStream_t st) {
@@ -497,7 +504,7 @@ cudaError_t launch_tc_compress(const CUtensorMap& map, const TcGeom& t, int fmt,
 }
 
 template <int FMT>
-static cudaError_t launch_exp_t(const TcGeom& t, const float2* H, const uint16_t* Bx, void* V, int rows,
+static cudaError_t launch_exp_t(const TcGeom& t, const float2* H, const uint16_t* Bx, float2* V, int rows,
                                 int* status, cudaStream_t st) {
   const size_t sm = tc_expand_smem(t);
   static size_t attr = 0;
@@ -506,11 +513,11 @@ static cudaError_t launch_exp_t(const TcGeom& t, const float2* H, const uint16_t
     attr = sm;
   }
   dim3 grid((rows + t.lt - 1) / t.lt, t.G);
-  note_launches(1); k_tc_expand<FMT><<<grid, kTcThreads, sm, st>>>(t, H, Bx, (uint32_t*)V, rows, status);
+  note_launches(1); k_tc_expand<FMT><<<grid, kTcThreads, sm, st>>>(t, H, Bx, V, rows, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_expand(const TcGeom& t, int fmt, const float2* H, const uint16_t* Bx, void* V, int rows,
+cudaError_t launch_tc_expand(const TcGeom& t, int fmt, const float2* H, const uint16_t* Bx, float2* V, int rows,
                              int* status, cudaStream_t st) {
   return fmt == 1 ? launch_exp_t<1>(t, H, Bx, V, rows, status, st) : launch_exp_t<0>(t, H, Bx, V, rows, status, st);
 }

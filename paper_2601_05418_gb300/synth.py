@@ -13,7 +13,8 @@ oversampling factors and wave parameters of Sec. 3.2 and SI Sec. 5):
               about 10x compression, R=3, CG 20 iterations.
 * ``2d256``   256x256, 32 coils, 8x oversampling, 32 groups, 16x, R=3,
               FISTA l1-Haar 50 iterations (FP32 operator).
-* ``2d256bf`` the same data with the BF16 tensor-core operator.
+* ``2d256h``  the same data with the FP16 tensor-core operator and
+              compression (``2d256bf``: BF16 operands).
 * ``batch64`` 64 uneven 2D slices (192..320, 16..32 coils, 6..8x, 16..48
               groups), CG 30 iterations each.
 * ``3d224``   224x224x160, 32 coils, corkscrew wave, 6x, 48 contiguous
@@ -262,11 +263,11 @@ def workload(name: str) -> Workload:
     if name == "2d128":
         g = _geom_2d(128, 8, 4, 8, 2.5, 16, 10.0, 3)
         return Workload(name, g, seed=1, alg="cg", iters=20)
-    if name in ("2d256", "2d256bf"):
+    if name in ("2d256", "2d256bf", "2d256h"):
         g = _geom_2d(256, 32, 8, 8, 2.5, 32, 16.0, 3)
+        prec = {"2d256": "fp32", "2d256bf": "bf16", "2d256h": "fp16"}[name]
         return Workload(name, g, seed=2, alg="fista", iters=50, lam=1e-3,
-                        haar_levels=4,
-                        precision="bf16" if name.endswith("bf") else "fp32")
+                        haar_levels=4, precision=prec)
     if name == "3d224":
         return Workload(name, geom_3d(224, 224, 160, 32, 6, 11, 6.0, 4.5, 48, 20.0),
                         seed=5, alg="cg", iters=10)
