@@ -221,6 +221,30 @@ typedef struct gpjc_recon_info {
 gpjc_status gpjc_recon(const gpjc_op* op, const float* d_Sc, float* d_x, const gpjc_recon_params* params,
                        gpjc_recon_info* info, void* stream);
 
+/* ------------------------------------------------------------------ batch -- */
+/* Many 2D slices (each with its own plan, groups and FP32 operator; sizes,
+ * coil counts, oversampling and groups may differ) reconstructed by CG in
+ * one persistent cooperative launch: every (slice, stage, tile) is a work
+ * item of a device queue, and an item waits (bounded) for the previous stage
+ * of its slice.  The slices' operators must not be used elsewhere while the
+ * batch runs.  Creation allocates the queue and counters (synchronous). */
+typedef struct gpjc_batch gpjc_batch;
+gpjc_status gpjc_batch_create(int32_t n, gpjc_op* const* ops, int32_t iters, gpjc_batch** out);
+void gpjc_batch_destroy(gpjc_batch* batch);
+/* CG with x0 = 0 and exactly `iters` iterations per slice (the recurrences
+ * of gpjc_recon with alg = GPJC_CG).  d_Sc[i] [n_lines_i][ntx_c_i] in,
+ * d_x[i] [ny_i][nx_i] out: host arrays of device pointers.  use_graph: replay
+ * a captured graph (memsets + the persistent kernel) while the pointers stay
+ * the same.  h_status (may be NULL): device status after a synchronisation. */
+gpjc_status gpjc_recon_batched(gpjc_batch* batch, const float* const* d_Sc, float* const* d_x, int32_t use_graph,
+                               int32_t* h_status, void* stream);
+/* Budget of each dependency wait in SM clock cycles (default 4e9, about 2 s);
+ * when a wait runs out the launch aborts and reports GPJC_ETIMEOUT.  Tests
+ * set a tiny budget to exercise that path without faulting anything. */
+gpjc_status gpjc_batch_set_wait_budget(gpjc_batch* batch, int64_t cycles);
+/* Blocks of the persistent launch and work items of one reconstruction. */
+gpjc_status gpjc_batch_info(const gpjc_batch* batch, int32_t* grid, int64_t* items);
+
 /* ------------------------------------------------------------------ no allocation -- */
 /* x = E_c^H y without any allocation: the paper has no counterpart; this
  * entry point exists for callers that cannot call cudaMalloc on the path

@@ -21,6 +21,9 @@
 
 using namespace gpjc;
 
+static constexpr int kVecChunkHost = 2048;  // vector elements per batch work item (k_readout.cu)
+static constexpr int kPeCBHost = 16;
+
 // ------------------------------------------------------------------ launches --
 #include <atomic>
 static std::atomic<unsigned long long> g_launches{0};
@@ -1174,5 +1177,215 @@ extern "C" gpjc_status gpjc_apply_EH_static(const gpjc_groups* gr, const float* 
   // H2 and T are fully overwritten before they are read: nothing to clear.
   CK(launch_pe_adj(g, (const float2*)d_y, g.ntxc, T, H2, st));
   CK(launch_k1_adj_fp32(g, H2, (const float2*)d_coil, gr->A, (float2*)d_x, 1, st));
+  return GPJC_OK;
+}
+
+// ------------------------------------------------------------------ batched CG --
+struct gpjc_batch {
+  int n, iters, n_stages, grid;
+  long long wait_cycles;
+  size_t smem;
+  std::vector<gpjc_op*> ops;
+  std::vector<BatchSlice> hs;      // host copy of the slice descriptors
+  std::vector<long long> stage_start;
+  std::vector<int> slice_off;
+  BatchSlice* d_slices;
+  long long* d_stage_start;
+  int* d_slice_off;
+  int* d_done;
+  unsigned long long* d_head;
+  int* d_abort;
+  int* d_status;
+  double* d_scal;                  // [n][2 iters + 1]
+  cudaGraphExec_t gexec;
+  std::vector<const void*> gkey;
+  DevMem mem;
+};
+
+extern "C" gpjc_status gpjc_batch_create(int32_t n, gpjc_op* const* ops, int32_t iters, gpjc_batch** out) {
+  if (!ops || !out || n < 1) return fail(GPJC_EINVAL, "need at least one operator");
+  if (iters < 0 || iters > 10000) return fail(GPJC_EINVAL, "iters out of range");
+  *out = nullptr;
+  auto* b = new (std::nothrow) gpjc_batch();
+  if (!b) return fail(GPJC_ENOMEM, "host allocation");
+  std::unique_ptr<gpjc_batch> guard(b);
+  b->n = n;
+  b->iters = iters;
+  b->n_stages = 3 + 5 * iters;
+  b->ops.assign(ops, ops + n);
+  b->hs.resize(n);
+  size_t smem = 0;
+  for (int i = 0; i < n; ++i) {
+    gpjc_op* op = ops[i];
+    if (!op) return fail(GPJC_EINVAL, "operator %d is null", i);
+    const gpjc_plan* p = op->plan;
+    const Geo& g = p->geo;
+    if (op->prec != GPJC_FP32) return fail(GPJC_EUNSUPPORTED, "batched CG runs the FP32 operator (slice %d)", i);
+    if (g.dim3d) return fail(GPJC_EUNSUPPORTED, "batched CG is 2D (slice %d)", i);
+    if (!p->rt_f.rb || !p->rt_a.rb || p->rt_f.nt > 512)
+      return fail(GPJC_EUNSUPPORTED, "slice %d has no register-tile plan for the batch kernel", i);
+    for (int j = 0; j < i; ++j)
+      if (ops[j] == op) return fail(GPJC_EINVAL, "operator %d appears twice", i);
+    BatchSlice& s = b->hs[i];
+    memset(&s, 0, sizeof s);
+    s.g = g;
+    s.rtf = p->rt_f;
+    s.rta = p->rt_a;
+    s.nchunk = op->nchunk;
+    s.cpc = (g.nc + op->nchunk - 1) / op->nchunk;
+    s.n_f = ((g.rows + p->rt_f.rb - 1) / p->rt_f.rb) * op->nchunk;
+    s.n_a = ((g.rows + p->rt_a.rb - 1) / p->rt_a.rb) * op->nchunk;
+    s.n_pe = (g.ntxc + kPeCBHost - 1) / kPeCBHost;
+    s.n_vec = (int)((op->L + kVecChunkHost - 1) / kVecChunkHost);
+    s.mt_f = (p->rt_f.nt + 255) / 256;
+    const int mx = (p->rt_a.rb * g.nx + 255) / 256;
+    s.mx_a = mx <= 1 ? 1 : mx <= 2 ? 2 : mx <= 4 ? 4 : 8;
+    if (mx > 8) return fail(GPJC_EUNSUPPORTED, "slice %d: adjoint rows too wide", i);
+    s.coil = op->coil;
+    s.AT = op->gr->AT;
+    s.A = op->gr->A;
+    s.Hpart = op->Hpart;
+    s.H2 = op->H2;
+    s.xparts = op->xparts;
+    s.r = op->vr;
+    s.p = op->vp;
+    smem = std::max(smem, std::max(readout_fwd_smem(g, p->rt_f.rb), readout_adj_smem(g, p->rt_a.rb)));
+    smem = std::max(smem, batch_pe_smem(g));
+  }
+  b->smem = smem;
+  // queue layout: stage-major, then slice, then item
+  const int types = 7;
+  b->slice_off.assign((size_t)types * (n + 1), 0);
+  for (int t = 0; t < types; ++t)
+    for (int i = 0; i < n; ++i) {
+      const BatchSlice& s = b->hs[i];
+      const int items = (t == 0 || t == 4) ? s.n_pe : (t == 1) ? s.n_a : (t == 3) ? s.n_f : s.n_vec;
+      b->slice_off[(size_t)t * (n + 1) + i + 1] = b->slice_off[(size_t)t * (n + 1) + i] + items;
+    }
+  b->stage_start.assign(b->n_stages + 1, 0);
+  for (int j = 0; j < b->n_stages; ++j) {
+    int t = j < 3 ? j : ((j - 3) % 5 == 0 ? 3 : (j - 3) % 5 == 1 ? 4 : (j - 3) % 5 == 2 ? 1 : (j - 3) % 5 == 3 ? 5 : 6);
+    b->stage_start[j + 1] = b->stage_start[j] + b->slice_off[(size_t)t * (n + 1) + n];
+  }
+  DevMem& m = b->mem;
+  gpjc_status s;
+  if ((s = m.alloc(&b->d_slices, n)) || (s = m.upload(&b->d_stage_start, b->stage_start)) ||
+      (s = m.upload(&b->d_slice_off, b->slice_off)) || (s = m.alloc(&b->d_done, (size_t)n * b->n_stages)) ||
+      (s = m.alloc(&b->d_head, 1)) || (s = m.alloc(&b->d_abort, 1)) || (s = m.alloc(&b->d_status, 1)) ||
+      (s = m.alloc(&b->d_scal, (size_t)n * (2 * iters + 1))))
+    return s;
+  for (int i = 0; i < n; ++i) {
+    b->hs[i].rr = b->d_scal + (size_t)i * (2 * iters + 1);
+    b->hs[i].qq = b->hs[i].rr + iters + 1;
+  }
+  b->wait_cycles = 4000000000ll;  // about 2 s at the maximum SM clock
+  b->grid = batch_max_blocks(smem);
+  if (b->grid < 1) return fail(GPJC_EUNSUPPORTED, "batch kernel does not fit on an SM (%zu B shared memory)", smem);
+  b->gexec = nullptr;
+  *out = guard.release();
+  return GPJC_OK;
+}
+
+extern "C" void gpjc_batch_destroy(gpjc_batch* b) {
+  if (!b) return;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  delete b;
+}
+
+static gpjc_status batch_body(gpjc_batch* b, cudaStream_t st) {
+  const int n = b->n;
+  CK(cudaMemsetAsync(b->d_done, 0, sizeof(int) * (size_t)n * b->n_stages, st));
+  CK(cudaMemsetAsync(b->d_head, 0, sizeof(unsigned long long), st));
+  CK(cudaMemsetAsync(b->d_abort, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(b->d_status, 0, sizeof(int), st));
+  CK(cudaMemsetAsync(b->d_scal, 0, sizeof(double) * (size_t)n * (2 * b->iters + 1), st));
+  BatchPlan bp;
+  bp.n_slices = n;
+  bp.n_stages = b->n_stages;
+  bp.slices = b->d_slices;
+  bp.stage_start = b->d_stage_start;
+  bp.slice_off = b->d_slice_off;
+  bp.done = b->d_done;
+  bp.head = b->d_head;
+  bp.abort = b->d_abort;
+  bp.status = b->d_status;
+  bp.wait_cycles = b->wait_cycles;
+  CK(launch_batch_cg(bp, b->grid, b->smem, st));
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_recon_batched(gpjc_batch* b, const float* const* d_Sc, float* const* d_x,
+                                          int32_t use_graph, int32_t* h_status, void* stream) {
+  if (!b || !d_Sc || !d_x) return fail(GPJC_EINVAL, "null argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<const void*> key(2 * b->n);
+  for (int i = 0; i < b->n; ++i) {
+    if (!d_Sc[i] || !d_x[i]) return fail(GPJC_EINVAL, "slice %d: null data pointer", i);
+    key[2 * i] = d_Sc[i];
+    key[2 * i + 1] = d_x[i];
+  }
+  const bool same = (key == b->gkey);
+  if (!same) {
+    for (int i = 0; i < b->n; ++i) {
+      b->hs[i].Sc = (const float2*)d_Sc[i];
+      b->hs[i].x = (float2*)d_x[i];
+    }
+    CK(cudaMemcpy(b->d_slices, b->hs.data(), sizeof(BatchSlice) * b->n, cudaMemcpyHostToDevice));
+    if (b->gexec) {
+      cudaGraphExecDestroy(b->gexec);
+      b->gexec = nullptr;
+    }
+    b->gkey = key;
+  }
+  gpjc_status s;
+  if (use_graph) {
+    if (!b->gexec) {
+      cudaStream_t cs;
+      CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      cudaGraph_t graph;
+      cudaError_t ce = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+      if (ce == cudaSuccess) {
+        g_capturing = true;
+        s = batch_body(b, cs);
+        g_capturing = false;
+        ce = cudaStreamEndCapture(cs, &graph);
+        if (!s && ce == cudaSuccess) {
+          ce = cudaGraphInstantiate(&b->gexec, graph, 0);
+          cudaGraphDestroy(graph);
+        }
+      }
+      cudaStreamDestroy(cs);
+      if (s) return s;
+      if (ce != cudaSuccess) return fail(GPJC_ECUDA, "batch graph: %s", cudaGetErrorString(ce));
+    }
+    CK(cudaGraphLaunch(b->gexec, st));
+    note_launches(1);
+  } else {
+    if ((s = batch_body(b, st))) return s;
+  }
+  if (h_status) {
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, b->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *h_status = v == kDevNonFinite ? GPJC_ENONFINITE : (v ? GPJC_ETIMEOUT : GPJC_OK);
+    if (v) return fail((gpjc_status)*h_status, "batched reconstruction device status %d", v);
+  }
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_batch_set_wait_budget(gpjc_batch* b, int64_t cycles) {
+  if (!b || cycles < 0) return fail(GPJC_EINVAL, "invalid argument");
+  b->wait_cycles = cycles;
+  if (b->gexec) {  // the budget is a kernel argument of the captured graph
+    cudaGraphExecDestroy(b->gexec);
+    b->gexec = nullptr;
+  }
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_batch_info(const gpjc_batch* b, int32_t* grid, int64_t* items) {
+  if (!b) return fail(GPJC_EINVAL, "null batch");
+  if (grid) *grid = b->grid;
+  if (items) *items = b->stage_start.back();
   return GPJC_OK;
 }

@@ -269,4 +269,92 @@ __device__ __forceinline__ bool grid_sum_finalize(double v, double* partials, un
   return false;
 }
 
+// ------------------------------------------------------------------ phase-encode (2D) --
+// A block owns kPeCB columns of the hybrid matrix [ny][ncols].  Centred
+// unitary DFT along y: F[ky,y] = (-1)^y (-1)^{ky + ny/2} e^{-2 pi i ky y/ny} / sqrt(ny).
+constexpr int kPeCB = 16;
+__device__ __forceinline__ float pe_sgn(int k) { return (k & 1) ? -1.0f : 1.0f; }
+
+// H = F_y^H M^T Sc for the columns of block `cb`.
+__device__ __forceinline__ void pe_adj2d_body(const Geo& g, const float2* __restrict__ Sc, int ncols,
+                                              float2* __restrict__ H, int cb, float2* smem) {
+  const int ny = g.ny, bs = ny + 1;
+  float2* a = smem;
+  float2* b = smem + kPeCB * bs;
+  float2* tw = smem + 2 * kPeCB * bs;
+  for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = g.tw_y[i];
+  for (int i = threadIdx.x; i < kPeCB * bs; i += blockDim.x) a[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const int col0 = cb * kPeCB;
+  for (int i = threadIdx.x; i < g.n_lines * kPeCB; i += blockDim.x) {
+    const int l = i / kPeCB, c = i - l * kPeCB;
+    const int col = col0 + c;
+    if (col < ncols) {
+      const int ky = g.line_ky[l];
+      a[c * bs + ky] = cscale(__ldg(Sc + (size_t)l * ncols + col), pe_sgn(ky + ny / 2) * g.inv_sqrt_ny);
+    }
+  }
+  __syncthreads();
+  float2* res = fft_batch<+1>(a, b, kPeCB, bs, g.fy, tw, threadIdx.x, blockDim.x);
+  for (int i = threadIdx.x; i < ny * kPeCB; i += blockDim.x) {
+    const int y = i / kPeCB, c = i - y * kPeCB;
+    const int col = col0 + c;
+    if (col < ncols) H[(size_t)y * ncols + col] = cscale(res[c * bs + y], pe_sgn(y));
+  }
+  __syncthreads();
+}
+
+// H2 = F_y^H M^T M F_y (sum over chunks of Hpart) for the columns of block
+// `cb`; returns the block's ||M F_y H||^2 (valid in thread 0).  With P the
+// hybrid partials are read with coherent loads.
+template <bool P>
+__device__ __forceinline__ double pe_normal2d_body(const Geo& g, const float2* __restrict__ Hpart, int nchunk,
+                                                   int ncols, float2* __restrict__ H2, int cb, float2* smem) {
+  __shared__ double red[32];
+  const int ny = g.ny, bs = ny + 1;
+  float2* a = smem;
+  float2* b = smem + kPeCB * bs;
+  float2* tw = smem + 2 * kPeCB * bs;
+  for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = g.tw_y[i];
+  const int col0 = cb * kPeCB;
+  const size_t plane = (size_t)g.rows * ncols;
+  for (int i = threadIdx.x; i < ny * kPeCB; i += blockDim.x) {
+    const int y = i / kPeCB, c = i - y * kPeCB;
+    const int col = col0 + c;
+    float2 v = make_float2(0.f, 0.f);
+    if (col < ncols)
+      for (int ch = 0; ch < nchunk; ++ch) {
+        const float2* src = Hpart + ch * plane + (size_t)y * ncols + col;
+        v = cadd(v, P ? __ldcg(src) : __ldg(src));
+      }
+    a[c * bs + y] = cscale(v, pe_sgn(y));
+  }
+  __syncthreads();
+  float2* res = fft_batch<-1>(a, b, kPeCB, bs, g.fy, tw, threadIdx.x, blockDim.x);
+  float2* oth = (res == a) ? b : a;
+  const float inv_ny = 1.0f / (float)ny;
+  double part = 0.0;
+  for (int i = threadIdx.x; i < ny * kPeCB; i += blockDim.x) {
+    const int c = i / ny, ky = i - c * ny;
+    float2 v = res[c * bs + ky];
+    if (g.line_of[ky] >= 0 && col0 + c < ncols) {
+      part += ((double)v.x * v.x + (double)v.y * v.y) * inv_ny;
+      v = cscale(v, inv_ny);
+    } else {
+      v = make_float2(0.f, 0.f);
+    }
+    res[c * bs + ky] = v;
+  }
+  __syncthreads();
+  float2* res2 = fft_batch<+1>(res, oth, kPeCB, bs, g.fy, tw, threadIdx.x, blockDim.x);
+  for (int i = threadIdx.x; i < ny * kPeCB; i += blockDim.x) {
+    const int y = i / kPeCB, c = i - y * kPeCB;
+    const int col = col0 + c;
+    if (col < ncols) H2[(size_t)y * ncols + col] = cscale(res2[c * bs + y], pe_sgn(y));
+  }
+  const double tot = block_sum(part, red);
+  __syncthreads();
+  return tot;
+}
+
 }  // namespace gpjc

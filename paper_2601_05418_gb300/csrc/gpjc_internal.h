@@ -72,6 +72,33 @@ struct TcGeom {
   const float* scale;
 };
 
+// One slice of a batched persistent CG reconstruction (k_readout.cu).
+struct BatchSlice {
+  Geo g;
+  RTiles rtf, rta;
+  int nchunk, cpc;
+  int n_f, n_a, n_pe, n_vec;  // items per stage type
+  int mt_f, mx_a;             // register-tile variants of the readout bodies
+  const float2* coil;
+  const float2* AT;
+  const float2* A;
+  const float2* Sc;
+  float2 *Hpart, *H2, *xparts, *x, *r, *p;
+  double* rr;  // [iters + 1] ||r||^2 per iteration
+  double* qq;  // [iters] ||E_c p||^2 per iteration
+};
+struct BatchPlan {
+  int n_slices, n_stages;
+  const BatchSlice* slices;
+  const long long* stage_start;  // [n_stages + 1] first queue item of each stage
+  const int* slice_off;          // [7][n_slices + 1] first item of each slice within a stage of a type
+  int* done;                     // [n_slices][n_stages] completed items
+  unsigned long long* head;      // next queue item
+  int* abort;
+  int* status;
+  long long wait_cycles;         // budget of one dependency wait (SM clock cycles)
+};
+
 // Device status word values (written by kernels, read by the host).
 enum DevStatus : int { kDevOk = 0, kDevNonFinite = 1, kDevTimeout = 2, kDevBadIndex = 3 };
 

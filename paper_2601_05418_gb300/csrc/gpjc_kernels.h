@@ -50,6 +50,11 @@ cudaError_t launch_k1f_tiled(const Geo& g, const RTiles& tl, const float2* x, co
 cudaError_t launch_k1a_tiled(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,
                              const float2* A, float2* xpart, int nchunk, cudaStream_t st);
 
+// ---- batched persistent CG (k_readout.cu)
+size_t batch_pe_smem(const Geo& g);
+cudaError_t launch_batch_cg(const BatchPlan& bp, int grid, size_t smem, cudaStream_t st);
+int batch_max_blocks(size_t smem);
+
 // ---- tensor-core compression (k_tc.cu)
 bool make_tc_tmap(const TcGeom& t, const void* base, int lines, int ebytes, CUtensorMap* map);
 size_t tc_compress_smem(const TcGeom& t);

@@ -329,29 +329,7 @@ __global__ void __launch_bounds__(kK2Threads) k2_fwd_2d(Geo g, const float2* __r
 __global__ void __launch_bounds__(kK2Threads) k2_adj_2d(Geo g, const float2* __restrict__ Sc, int ncols,
                                                         float2* __restrict__ H) {
   extern __shared__ float2 smem[];
-  const int ny = g.ny, bs = ny + 1;
-  float2* a = smem;
-  float2* b = smem + kCB * bs;
-  float2* tw = smem + 2 * kCB * bs;
-  for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = g.tw_y[i];
-  for (int i = threadIdx.x; i < kCB * bs; i += blockDim.x) a[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  const int col0 = blockIdx.x * kCB;
-  for (int i = threadIdx.x; i < g.n_lines * kCB; i += blockDim.x) {
-    const int l = i / kCB, c = i - l * kCB;
-    const int col = col0 + c;
-    if (col < ncols) {
-      const int ky = g.line_ky[l];
-      a[c * bs + ky] = cscale(Sc[(size_t)l * ncols + col], sgn(ky + ny / 2) * g.inv_sqrt_ny);
-    }
-  }
-  __syncthreads();
-  float2* res = fft_batch<+1>(a, b, kCB, bs, g.fy, tw, threadIdx.x, blockDim.x);
-  for (int i = threadIdx.x; i < ny * kCB; i += blockDim.x) {
-    const int y = i / kCB, c = i - y * kCB;
-    const int col = col0 + c;
-    if (col < ncols) H[(size_t)y * ncols + col] = cscale(res[c * bs + y], sgn(y));
-  }
+  pe_adj2d_body(g, Sc, ncols, H, blockIdx.x, smem);
 }
 
 // 2D normal: H2 = F_y^H M^T M F_y (sum_chunk Hpart); ||M F_y H||^2 reduced
@@ -362,45 +340,9 @@ __global__ void __launch_bounds__(kK2Threads) k2_normal_2d(Geo g, const float2* 
                                                            unsigned* counter, double* qq) {
   extern __shared__ float2 smem[];
   __shared__ double red[32];
-  const int ny = g.ny, bs = ny + 1;
-  float2* a = smem;
-  float2* b = smem + kCB * bs;
-  float2* tw = smem + 2 * kCB * bs;
-  for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = g.tw_y[i];
-  const int col0 = blockIdx.x * kCB;
-  const size_t plane = (size_t)g.rows * ncols;
-  for (int i = threadIdx.x; i < ny * kCB; i += blockDim.x) {
-    const int y = i / kCB, c = i - y * kCB;
-    const int col = col0 + c;
-    float2 v = make_float2(0.f, 0.f);
-    if (col < ncols)
-      for (int ch = 0; ch < nchunk; ++ch) v = cadd(v, Hpart[ch * plane + (size_t)y * ncols + col]);
-    a[c * bs + y] = cscale(v, sgn(y));
-  }
-  __syncthreads();
-  float2* res = fft_batch<-1>(a, b, kCB, bs, g.fy, tw, threadIdx.x, blockDim.x);
-  float2* oth = (res == a) ? b : a;
-  const float inv_ny = 1.0f / (float)ny;
-  double part = 0.0;
-  for (int i = threadIdx.x; i < ny * kCB; i += blockDim.x) {
-    const int c = i / ny, ky = i - c * ny;
-    float2 v = res[c * bs + ky];
-    if (g.line_of[ky] >= 0 && col0 + c < ncols) {
-      part += ((double)v.x * v.x + (double)v.y * v.y) * inv_ny;
-      v = cscale(v, inv_ny);
-    } else {
-      v = make_float2(0.f, 0.f);
-    }
-    res[c * bs + ky] = v;
-  }
-  __syncthreads();
-  float2* res2 = fft_batch<+1>(res, oth, kCB, bs, g.fy, tw, threadIdx.x, blockDim.x);
-  for (int i = threadIdx.x; i < ny * kCB; i += blockDim.x) {
-    const int y = i / kCB, c = i - y * kCB;
-    const int col = col0 + c;
-    if (col < ncols) H2[(size_t)y * ncols + col] = cscale(res2[c * bs + y], sgn(y));
-  }
-  if (qq) grid_sum_finalize(part, partials, counter, qq, red);
+  const double tot = pe_normal2d_body<false>(g, Hpart, nchunk, ncols, H2, blockIdx.x, smem);
+  // the block total is valid in thread 0 only
+  if (qq) grid_sum_finalize(threadIdx.x == 0 ? tot : 0.0, partials, counter, qq, red);
 }
 
 // ---- 3D: y pass over (z, column slab), z pass over (ky, column slab).

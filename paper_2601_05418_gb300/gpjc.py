@@ -96,6 +96,11 @@ _sig("gpjc_simulate", [_P, _P, _P, _P])
 _sig("gpjc_simulate_adjoint", [_P, _P, _P, _P])
 _sig("gpjc_recon", [_P, _P, _P, C.POINTER(ReconParams), C.POINTER(ReconInfo), _P])
 _sig("gpjc_apply_EH_static", [_P, _P, _P, _P, _P])
+_sig("gpjc_batch_create", [C.c_int32, C.POINTER(_P), C.c_int32, C.POINTER(_P)])
+_sig("gpjc_batch_destroy", [_P], None)
+_sig("gpjc_recon_batched", [_P, C.POINTER(_P), C.POINTER(_P), C.c_int32, _I32P, _P])
+_sig("gpjc_batch_set_wait_budget", [_P, C.c_int64])
+_sig("gpjc_batch_info", [_P, _I32P, C.POINTER(C.c_int64)])
 
 
 def check(status: int) -> None:
@@ -359,6 +364,42 @@ def apply_EH_static(groups: Groups, coil: torch.Tensor, y: torch.Tensor, out=Non
     check(_lib.gpjc_apply_EH_static(groups.h, _dptr(coil, torch.complex64), _dptr(y, torch.complex64),
                                     _dptr(out, torch.complex64), _stream(stream)))
     return out
+
+
+class Batch:
+    """Batched CG over many FP32 operators in one persistent launch."""
+
+    def __init__(self, ops: Sequence[Operator], iters: int):
+        self.ops = list(ops)
+        arr = (_P * len(self.ops))(*[op.h for op in self.ops])
+        self.h = _P()
+        check(_lib.gpjc_batch_create(len(self.ops), arr, iters, C.byref(self.h)))
+        self.iters = iters
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.gpjc_batch_destroy(self.h)
+            self.h = None
+
+    def info(self):
+        grid, items = C.c_int32(), C.c_int64()
+        check(_lib.gpjc_batch_info(self.h, C.byref(grid), C.byref(items)))
+        return grid.value, items.value
+
+    def set_wait_budget(self, cycles: int) -> None:
+        check(_lib.gpjc_batch_set_wait_budget(self.h, cycles))
+
+    def recon(self, Scs: Sequence[torch.Tensor], xs: Optional[Sequence[torch.Tensor]] = None,
+              use_graph: bool = True, sync: bool = True, stream=None):
+        if xs is None:
+            xs = [torch.empty(op.image_shape, dtype=torch.complex64, device=Sc.device)
+                  for op, Sc in zip(self.ops, Scs)]
+        sp = (_P * len(Scs))(*[_dptr(t, torch.complex64) for t in Scs])
+        xp = (_P * len(xs))(*[_dptr(t, torch.complex64) for t in xs])
+        st = C.c_int32(0)
+        check(_lib.gpjc_recon_batched(self.h, sp, xp, 1 if use_graph else 0, C.byref(st) if sync else None,
+                                      _stream(stream)))
+        return xs, st.value
 
 
 def plan_from(geom) -> Plan:
