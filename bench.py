@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpjc", choices=["gpjc", "reference"])
-    ap.add_argument("--workload", default="2d256", choices=["2d256", "2d256h", "2d256bf", "2d128"])
+    ap.add_argument("--workload", default="2d256", choices=["2d256", "2d256h", "2d256bf", "2d128", "batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -373,11 +373,100 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args, rank, world, local):
+    """64 uneven 2D slices, CG-SENSE 30 iterations each, in one persistent
+    launch replayed from a CUDA graph; the same slices reconstructed one
+    after another with the single-slice path are timed beside it."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_05418_gb300 import gpjc, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wls = synth.batch_workloads(64)
+    ops, scs, xs, keep = [], [], [], []
+    gen = torch.Generator(device=dev).manual_seed(4)
+    for wl in wls:
+        g = wl.geom
+        rho = synth.phantom(g.nx, g.ny)
+        coils = synth.coil_maps(g.nx, g.ny, 1, g.nc, wl.seed)
+        plan = gpjc.Plan(g)
+        c_d = torch.from_numpy(coils.astype(np.complex64)).to(dev)
+        grp = gpjc.Groups.build(plan, c_d, torch.from_numpy(synth.roi_mask(rho)).to(dev))
+        op = gpjc.Operator(grp, c_d)
+        op.autotune()
+        S = op.simulate(torch.from_numpy(rho.astype(np.complex64)).to(dev))
+        S += wl.sigma / np.sqrt(2) * torch.complex(torch.randn(S.shape, generator=gen, device=dev),
+                                                    torch.randn(S.shape, generator=gen, device=dev))
+        scs.append(gpjc.compress(grp, S))
+        xs.append(torch.empty(g.shape, dtype=torch.complex64, device=dev))
+        ops.append(op)
+        keep.append((plan, grp, c_d))
+    iters = wls[0].iters
+    batch = gpjc.Batch(ops, iters)
+    grid, items = batch.info()
+    for _ in range(max(3, args.warmup)):
+        batch.recon(scs, xs, sync=False)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    sampler = ClockSampler(local)
+    sampler.start()
+    l0 = gpjc.launch_count()
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.recon(scs, xs, sync=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    launches = gpjc.launch_count() - l0
+    # the same work through the single-slice entry point, one slice after another
+    for op, sc, x in zip(ops, scs, xs):
+        op.recon(sc, alg=gpjc.CG, iters=iters, out=x, sync=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for op, sc, x in zip(ops, scs, xs):
+        op.recon(sc, alg=gpjc.CG, iters=iters, out=x, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    ms = tot / args.steps
+    pairs = len(ops) * iters
+    out = {"metric": METRIC + " (uneven 64-slice batch, CG-SENSE 30)", "value": round(pairs / (ms / 1e3), 2),
+           "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+           "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batch64", "slices": len(ops), "iters": iters,
+                      "sizes": sorted(set(int(w.geom.nx) for w in wls)),
+                      "coils": sorted(set(int(w.geom.nc) for w in wls)),
+                      "os": sorted(set(int(w.geom.os) for w in wls)),
+                      "groups": sorted(set(int(w.geom.n_groups) for w in wls)),
+                      "persistent_grid": grid, "work_items": items,
+                      "l2": "flushed (256 MB write) between timed steps"},
+           "sequential_single_slice_ms": round(seq_ms, 3),
+           "speedup_vs_sequential": round(seq_ms / ms, 3),
+           "recon_s_per_slice": round(ms / 1e3 / len(ops), 6),
+           "clocks": clocks, "gpu_launches": int(launches)}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch64":
+        run_batch(args, rank, world, local)
         return
     run_gpjc(args, rank, world, local)
 

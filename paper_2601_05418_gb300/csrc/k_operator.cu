@@ -225,20 +225,45 @@ __device__ __forceinline__ float2 load_v<__nv_bfloat162>(const __nv_bfloat162* p
   return __bfloat1622float2(*p);
 }
 
+// smem: two padded ntx buffers + twiddles; post / pre are read from their
+// global tables (L2 / L1 resident) in coalesced order
+static size_t sim_smem(const Geo& g) { return sizeof(float2) * (size_t)(2 * spad_size(g.ntx) + g.nx); }
+
+__device__ __forceinline__ float2 post_of(const Geo& g, int t, int row) {
+  const int y = row % g.ny, z = row / g.ny;
+  const float2 py = __ldg(g.post_y + (size_t)y * g.ntx + t);
+  if (g.nz == 1) return py;
+  return cmul(py, __ldg(g.post_z + (size_t)z * g.ntx + t));
+}
+
 template <typename VT>
 __global__ void __launch_bounds__(kK1Threads) k1_sim_fwd(Geo g, const float2* __restrict__ x,
                                                          const float2* __restrict__ coil,
                                                          VT* __restrict__ V, int cpc) {
   extern __shared__ float2 smem[];
+  float2* A = smem;
+  float2* B = A + spad_size(g.ntx);
+  float2* tw = B + spad_size(g.ntx);
   const int row = blockIdx.x, chunk = blockIdx.y;
-  const K1Smem sm = k1_smem_setup(g, row, smem);
+  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) tw[i] = g.tw_x[i];
   const size_t L = (size_t)g.rows * g.nx;
+  const int nx = g.nx, os = g.os;
+  const float2* xrow = x + (size_t)row * nx;
   const int n0 = chunk * cpc;
   const int n1 = min(g.nc, n0 + cpc);
   for (int n = n0; n < n1; ++n) {
-    const float2* U = k1_readout_fwd(g, sm, coil + n * L + (size_t)row * g.nx, x + (size_t)row * g.nx);
+    const float2* crow = coil + n * L + (size_t)row * nx;
+    for (int i = threadIdx.x; i < g.ntx; i += blockDim.x) {
+      const int xx = i % nx;
+      A[spad(i)] = cmul(cmul(__ldg(crow + xx), __ldg(xrow + xx)), __ldg(g.pre + i));
+    }
+    __syncthreads();
+    const float2* R = fft_batch<-1, true>(A, B, os, nx, g.fx, tw, threadIdx.x, blockDim.x);
     VT* out = V + ((size_t)row * g.nc + n) * g.ntx;
-    for (int t = threadIdx.x; t < g.ntx; t += blockDim.x) store_v<VT>(out + t, U[t]);
+    for (int t = threadIdx.x; t < g.ntx; t += blockDim.x) {
+      const int m = t / os, s = t - m * os;
+      store_v<VT>(out + t, cmul(R[spad(s * nx + m)], post_of(g, t, row)));
+    }
     __syncthreads();
   }
 }
@@ -248,8 +273,11 @@ __global__ void __launch_bounds__(kK1Threads) k1_sim_adj(Geo g, const VT* __rest
                                                          const float2* __restrict__ coil,
                                                          float2* __restrict__ xpart, int cpc) {
   extern __shared__ float2 smem[];
+  float2* A = smem;
+  float2* B = A + spad_size(g.ntx);
+  float2* tw = B + spad_size(g.ntx);
   const int row = blockIdx.x, chunk = blockIdx.y;
-  const K1Smem sm = k1_smem_setup(g, row, smem);
+  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) tw[i] = g.tw_x[i];
   const size_t L = (size_t)g.rows * g.nx;
   const int nx = g.nx, os = g.os;
   float2 xacc[MAXX];
@@ -260,20 +288,19 @@ __global__ void __launch_bounds__(kK1Threads) k1_sim_adj(Geo g, const VT* __rest
   for (int n = n0; n < n1; ++n) {
     const VT* vin = V + ((size_t)row * g.nc + n) * g.ntx;
     for (int t = threadIdx.x; t < g.ntx; t += blockDim.x) {
-      float2 v = cmulc(sm.post[t], load_v<VT>(vin + t));
       const int m = t / os, s = t - m * os;
-      sm.b[s * nx + m] = v;
+      A[spad(s * nx + m)] = cmulc(post_of(g, t, row), load_v<VT>(vin + t));
     }
     __syncthreads();
-    float2* res = k1_readout_adj_fft(g, sm);
+    const float2* R = fft_batch<+1, true>(A, B, os, nx, g.fx, tw, threadIdx.x, blockDim.x);
     const float2* crow = coil + n * L + (size_t)row * nx;
 #pragma unroll
     for (int j = 0; j < MAXX; ++j) {
       const int xx = threadIdx.x + j * kK1Threads;
       if (xx < nx) {
         float2 u = make_float2(0.f, 0.f);
-        for (int s = 0; s < os; ++s) cfmac(u, sm.pre[s * nx + xx], res[s * nx + xx]);
-        cfmac(xacc[j], crow[xx], u);
+        for (int s = 0; s < os; ++s) cfmac(u, __ldg(g.pre + s * nx + xx), R[spad(s * nx + xx)]);
+        cfmac(xacc[j], __ldg(crow + xx), u);
       }
     }
     __syncthreads();
@@ -526,7 +553,7 @@ static cudaError_t launch_sim_fwd_t(const Geo& g, const float2* x, const float2*
                                     cudaStream_t st) {
   const int cpc = (g.nc + nchunk - 1) / nchunk;
   dim3 grid(g.rows, nchunk);
-  const size_t sm = k1_smem_bytes(g);
+  const size_t sm = sim_smem(g);
   cudaFuncSetAttribute(k1_sim_fwd<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   note_launches(1); k1_sim_fwd<VT><<<grid, kK1Threads, sm, st>>>(g, x, coil, V, cpc);
   return cudaGetLastError();
@@ -537,7 +564,7 @@ static cudaError_t launch_sim_adj_t(const Geo& g, const VT* V, const float2* coi
                                     cudaStream_t st) {
   const int cpc = (g.nc + nchunk - 1) / nchunk;
   dim3 grid(g.rows, nchunk);
-  const size_t sm = k1_smem_bytes(g);
+  const size_t sm = sim_smem(g);
   if (g.nx <= kK1Threads) {
     cudaFuncSetAttribute(k1_sim_adj<VT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     note_launches(1); k1_sim_adj<VT, 1><<<grid, kK1Threads, sm, st>>>(g, V, coil, xpart, cpc);
