@@ -106,15 +106,17 @@ gpjc_status gpjc_plan_tables(const gpjc_plan* plan, int32_t* h_off, int32_t* h_r
 
 /* ------------------------------------------------------------------ groups -- */
 typedef struct gpjc_build_params {
-  int32_t eig_iters;    /* subspace iterations (0 = default 12)                   */
-  int32_t block;        /* subspace block size b (0 = default: min(N_s, max(2 keep, keep + 16), 96)) */
-  int32_t keep_gram;    /* keep P_g (FP64) for gpjc_groups_gram                    */
+  int32_t eig_iters;      /* FP64 subspace iterations (0 = default 3)                        */
+  int32_t block;          /* subspace block size b (0 = default: min(N_s, max(2 keep, keep + 16), 96)) */
+  int32_t keep_gram;      /* keep P_g (FP64) for gpjc_groups_gram                             */
+  int32_t eig_iters_fp32; /* FP32 iterations before the FP64 ones (0 = default 10, -1 = none) */
 } gpjc_build_params;
 
 /* Builds every group's compression matrix from coil maps and a ROI
  * (Sec. 2.4 steps 1-2, Eq. 6-12): ROI compaction (raster order, pixels that
  * no coil sees are dropped), Gram P_g in FP64 from the group's first patch,
- * leading eigenvectors by FP64 subspace iteration + Rayleigh-Ritz,
+ * leading eigenvectors by subspace iteration (FP32 iterations on a rounded
+ * copy of P_g, then FP64 iterations on P_g) + FP64 Rayleigh-Ritz,
  * A_g = C_g U_g^H (T (x) I_w).
  *   d_coil  [nc][nz][ny][nx] complex64, device
  *   d_roi   [nz][ny][nx] uint8 (nonzero = inside), device

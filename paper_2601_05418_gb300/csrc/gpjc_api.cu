@@ -370,7 +370,8 @@ struct gpjc_groups {
   double2* P;       // [G][ns][ns]
   bool built;       // from coil maps (vs. from matrices)
   bool keep_gram;
-  int b, iters, nblk, Kpad;
+  int b, iters, iters32, nblk, Kpad;
+  float2 *P32, *X32, *Y32;  // FP32 phase of the subspace iteration
   // scratch kept for rebuilds, so a rebuild allocates nothing and does
   // not synchronise
   int *blockcount, *blockoff, *d_ref;
@@ -436,6 +437,19 @@ static gpjc_status groups_compute(gpjc_groups* gr, const float2* coil, const uin
   CK(launch_hermitize(g, gr->P, st));
   double2 *X = gr->X, *Y = gr->Y;
   CK(launch_eig_init(g, b, X, st));
+  if (gr->iters32 > 0) {
+    // single-precision iterations first (64x the FP64 rate), then FP64 ones
+    const size_t nb = (size_t)g.G * g.ns * b;
+    CK(launch_to_f32(gr->P, gr->P32, (size_t)g.G * g.ns * g.ns, st));
+    CK(launch_to_f32(X, gr->X32, nb, st));
+    float2 *X32 = gr->X32, *Y32 = gr->Y32;
+    for (int it = 0; it < gr->iters32; ++it) {
+      CK(launch_eig_matmul32(g, b, gr->P32, X32, Y32, st));
+      CK(launch_eig_orth32(g, b, Y32, st));
+      std::swap(X32, Y32);
+    }
+    CK(launch_to_f64(X32, X, nb, st));
+  }
   for (int it = 0; it < gr->iters; ++it) {
     CK(launch_eig_matmul(g, b, gr->P, X, Y, st));
     CK(launch_eig_orth(g, b, Y, st));
@@ -482,9 +496,10 @@ extern "C" gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_c
   *out = nullptr;
   cudaStream_t st = (cudaStream_t)stream;
   const Geo& g = plan->geo;
-  gpjc_build_params bp = {0, 0, 0};
+  gpjc_build_params bp = {0, 0, 0, 0};
   if (params) bp = *params;
   if (bp.eig_iters < 0 || bp.eig_iters > 1000) return fail(GPJC_EINVAL, "eig_iters out of range");
+  if (bp.eig_iters_fp32 < -1 || bp.eig_iters_fp32 > 1000) return fail(GPJC_EINVAL, "eig_iters_fp32 out of range");
   int b = bp.block;
   if (b <= 0) b = std::min(plan->ns, std::min(96, std::max(2 * plan->keep_max, plan->keep_max + 16)));
   if (b < plan->keep_max || b > plan->ns) return fail(GPJC_EINVAL, "block %d must be in [keep_max, N_s]", b);
@@ -494,7 +509,8 @@ extern "C" gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_c
   std::unique_ptr<gpjc_groups> guard(gr);
   gr->plan = plan;
   gr->b = b;
-  gr->iters = bp.eig_iters > 0 ? bp.eig_iters : 12;
+  gr->iters = bp.eig_iters > 0 ? bp.eig_iters : 3;
+  gr->iters32 = bp.eig_iters_fp32 > 0 ? bp.eig_iters_fp32 : (bp.eig_iters_fp32 < 0 ? 0 : 10);
   gr->keep_gram = bp.keep_gram != 0;
   gr->built = true;
   gr->host_valid = false;
@@ -511,7 +527,9 @@ extern "C" gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_c
       (s = m.alloc(&gr->P, (size_t)g.G * g.ns * g.ns)) || (s = m.alloc(&gr->X, nb)) || (s = m.alloc(&gr->Y, nb)) ||
       (s = m.alloc(&gr->U, nb)) || (s = m.alloc(&gr->Hm, (size_t)g.G * b * b)) ||
       (s = m.alloc(&gr->W, (size_t)g.G * b * b)) || (s = m.alloc(&gr->ritz, (size_t)g.G * b)) ||
-      (s = m.alloc(&gr->order, (size_t)g.G * b)) || (s = m.alloc(&gr->resid, (size_t)g.G)))
+      (s = m.alloc(&gr->order, (size_t)g.G * b)) || (s = m.alloc(&gr->resid, (size_t)g.G)) ||
+      (s = m.alloc(&gr->P32, (size_t)g.G * g.ns * g.ns)) || (s = m.alloc(&gr->X32, nb)) ||
+      (s = m.alloc(&gr->Y32, nb)))
     return s;
   CK(cudaMemcpy(gr->d_ref, plan->ref.data(), sizeof(int) * g.G, cudaMemcpyHostToDevice));
   if ((s = groups_compute(gr, (const float2*)d_coil, d_roi, h_T, st))) return s;

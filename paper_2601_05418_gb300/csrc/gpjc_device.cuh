@@ -142,6 +142,14 @@ __host__ __device__ constexpr int spad_size(int n) { return n + (n >> 3) + 1; }
 // One Stockham stage of radix R on `batch` contiguous transforms of length n.
 // tw[k] = exp(-2 pi i k / n) for k < n.  With PAD, element i of the logical
 // buffer lives at spad(i).
+// floor(a / d) for a, d < 2^16 by one high multiply (magic = ceil(2^32 / d)):
+// the rounding error of the magic is below 2^-16 <= 1/d, so it never
+// carries the quotient across an integer.
+__device__ __forceinline__ unsigned fdiv_magic(unsigned d) {
+  return (unsigned)((0x100000000ull + d - 1) / d);
+}
+__device__ __forceinline__ int fdiv(int a, unsigned magic) { return (int)__umulhi((unsigned)a, magic); }
+
 template <int R, int SIGN, bool PAD = false>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, float2* __restrict__ dst,
                                                int n, int batch, int bs, int ns,
@@ -149,12 +157,14 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
   const int m = n / R;
   const int total = batch * m;
   const int twstep = n / (ns * R);
+  const unsigned mg_m = fdiv_magic((unsigned)m), mg_ns = fdiv_magic((unsigned)ns);
   for (int idx = tid; idx < total; idx += nthr) {
-    const int f = idx / m;
+    const int f = fdiv(idx, mg_m);
     const int j = idx - f * m;
     const int sb = f * bs;
     float2 v[R];
-    const int k = j % ns;
+    const int jq = fdiv(j, mg_ns);
+    const int k = j - jq * ns;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int li = sb + j + r * m;
@@ -173,7 +183,7 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
     if (R == 5) dft5<SIGN>(v);
     if (R == 7) dft7<SIGN>(v);
     if (R == 8) dft8<SIGN>(v);
-    const int base = sb + (j / ns) * ns * R + k;
+    const int base = sb + jq * ns * R + k;
 #pragma unroll
     for (int q = 0; q < R; ++q) {
       const int lo = base + q * ns;

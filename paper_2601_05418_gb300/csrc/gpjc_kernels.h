@@ -86,6 +86,10 @@ cudaError_t launch_eig_init(const Geo& g, int b, double2* X, cudaStream_t st);
 cudaError_t launch_eig_matmul(const Geo& g, int b, const double2* P, const double2* X, double2* Y,
                               cudaStream_t st);
 cudaError_t launch_eig_orth(const Geo& g, int b, double2* Y, cudaStream_t st);
+cudaError_t launch_to_f32(const double2* a, float2* b, size_t n, cudaStream_t st);
+cudaError_t launch_to_f64(const float2* a, double2* b, size_t n, cudaStream_t st);
+cudaError_t launch_eig_matmul32(const Geo& g, int b, const float2* P, const float2* X, float2* Y, cudaStream_t st);
+cudaError_t launch_eig_orth32(const Geo& g, int b, float2* Y, cudaStream_t st);
 cudaError_t launch_eig_project(const Geo& g, int b, const double2* Q, const double2* Z, double2* Hm,
                                cudaStream_t st);
 cudaError_t launch_eig_jacobi(const Geo& g, int b, double2* Hm, double2* W, double* ritz, int* order,

@@ -280,10 +280,11 @@ __global__ void __launch_bounds__(256) k_gram(Geo g, const float2* __restrict__ 
                                               const int* __restrict__ pix, const int* __restrict__ dK,
                                               int Kpad, const int* __restrict__ pref,
                                               double2* __restrict__ P) {
-  extern __shared__ float2 gsm[];
-  float2* As = gsm;                  // [kGKC][kGT]
-  float2* Bs = As + kGKC * kGT;      // [kGKC][kGT]
-  float2* psi = Bs + kGKC * kGT;     // [w][kGKC]
+  extern __shared__ __align__(16) unsigned char gsm_raw[];
+  double2* acc64 = (double2*)gsm_raw;              // [kGT * kGT] FP64 sums, thread-owned slots
+  float2* As = (float2*)(acc64 + kGT * kGT);      // [kGKC][kGT]
+  float2* Bs = As + kGKC * kGT;                   // [kGKC][kGT]
+  float2* psi = Bs + kGKC * kGT;                  // [w][kGKC]
   const int grp = blockIdx.y;
   // tile pair (I <= J) from the linear index
   const int nt = (g.ns + kGT - 1) / kGT;
@@ -299,16 +300,15 @@ __global__ void __launch_bounds__(256) k_gram(Geo g, const float2* __restrict__ 
   const int k_begin = blockIdx.z * kGSlab;
   const int k_end = min(((K + kGKC - 1) / kGKC) * kGKC, k_begin + kGSlab);
   if (k_begin >= k_end) return;
-
-  float2 acc[4][4];
-  double2 acc64[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      acc[a][b] = make_float2(0.f, 0.f);
-      acc64[a][b] = make_double2(0.0, 0.0);
-    }
+    for (int b = 0; b < 4; ++b) acc64[(ty * 4 + a) * kGT + tx * 4 + b] = make_double2(0.0, 0.0);
+  float2 acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = make_float2(0.f, 0.f);
   int run = 0;
   const float inv_ny = 1.0f / (float)g.ny;
   const float inv_nz = 1.0f / (float)g.nz;
@@ -363,14 +363,15 @@ __global__ void __launch_bounds__(256) k_gram(Geo g, const float2* __restrict__ 
         for (int b = 0; b < 4; ++b) cfmac(acc[a][b], bv[b], av[a]);  // a * conj(b)
     }
     __syncthreads();
-    if (++run == kGFlush) {
+    if (++run == kGFlush || k0 + kGKC >= k_end) {
       run = 0;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-          acc64[a][b].x += acc[a][b].x;
-          acc64[a][b].y += acc[a][b].y;
+          double2& d = acc64[(ty * 4 + a) * kGT + tx * 4 + b];
+          d.x += acc[a][b].x;
+          d.y += acc[a][b].y;
           acc[a][b] = make_float2(0.f, 0.f);
         }
     }
@@ -382,9 +383,10 @@ __global__ void __launch_bounds__(256) k_gram(Geo g, const float2* __restrict__ 
     for (int b = 0; b < 4; ++b) {
       const int i = I * kGT + ty * 4 + a, j = J * kGT + tx * 4 + b;
       if (i < g.ns && j < g.ns && i <= j) {
+        const double2 v = acc64[(ty * 4 + a) * kGT + tx * 4 + b];
         double2* d = Pg + (size_t)i * g.ns + j;
-        atomicAdd(&d->x, acc64[a][b].x + acc[a][b].x);
-        atomicAdd(&d->y, acc64[a][b].y + acc[a][b].y);
+        atomicAdd(&d->x, v.x);
+        atomicAdd(&d->y, v.y);
       }
     }
 }
@@ -408,8 +410,9 @@ cudaError_t launch_gram(const Geo& g, const float2* chat, const int* pix, const 
   const int nt = (g.ns + kGT - 1) / kGT;
   const int npairs = nt * (nt + 1) / 2;
   const int nslab = (Kpad + kGSlab - 1) / kGSlab;
-  const size_t sm = sizeof(float2) * (size_t)(2 * kGKC * kGT + g.w * kGKC);
+  const size_t sm = sizeof(double2) * (size_t)kGT * kGT + sizeof(float2) * (size_t)(2 * kGKC * kGT + g.w * kGKC);
   cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(k_gram, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   note_launches(1); k_gram<<<dim3(npairs, g.G, nslab), 256, sm, st>>>(g, chat, pix, dK, Kpad, pref, P);
   return cudaGetLastError();
 }
@@ -522,7 +525,140 @@ cudaError_t launch_eig_matmul(const Geo& g, int b, const double2* P, const doubl
                               cudaStream_t st) {
   if (b > kEigMaxB) return cudaErrorInvalidValue;
   const size_t sm = sizeof(double2) * (size_t)kMMK * b;
+  cudaFuncSetAttribute(k_eig_matmul, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   note_launches(1); k_eig_matmul<<<dim3((g.ns + kMMRows - 1) / kMMRows, g.G), 256, sm, st>>>(g.ns, b, P, X, Y);
+  return cudaGetLastError();
+}
+
+// ---- FP32 phase of the subspace iteration (same algorithm in single
+// precision; the FP64 iterations that follow refine its subspace)
+__global__ void k_to_f32(const double2* __restrict__ a, float2* __restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = make_float2((float)a[i].x, (float)a[i].y);
+}
+__global__ void k_to_f64(const float2* __restrict__ a, double2* __restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = make_double2((double)a[i].x, (double)a[i].y);
+}
+cudaError_t launch_to_f32(const double2* a, float2* b, size_t n, cudaStream_t st) {
+  note_launches(1); k_to_f32<<<1024, 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_to_f64(const float2* a, double2* b, size_t n, cudaStream_t st) {
+  note_launches(1); k_to_f64<<<1024, 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_eig_matmul32(int ns, int b, const float2* __restrict__ P,
+                                                      const float2* __restrict__ X, float2* __restrict__ Y) {
+  __shared__ float2 Ps[kMMRows][kMMK + 1];
+  extern __shared__ float2 Xs32[];  // [kMMK][b]
+  const int grp = blockIdx.y;
+  const float2* Pg = P + (size_t)grp * ns * ns;
+  const float2* Xg = X + (size_t)grp * ns * b;
+  float2* Yg = Y + (size_t)grp * ns * b;
+  const int r0 = blockIdx.x * kMMRows;
+  constexpr int MAXO = kMMRows * kEigMaxB / 256;
+  float2 acc[MAXO];
+#pragma unroll
+  for (int j = 0; j < MAXO; ++j) acc[j] = make_float2(0.f, 0.f);
+  const int nout = kMMRows * b;
+  for (int k0 = 0; k0 < ns; k0 += kMMK) {
+    for (int i = threadIdx.x; i < kMMRows * kMMK; i += blockDim.x) {
+      const int r = i / kMMK, kk = i - r * kMMK;
+      const int gr = r0 + r, gk = k0 + kk;
+      Ps[r][kk] = (gr < ns && gk < ns) ? Pg[(size_t)gr * ns + gk] : make_float2(0.f, 0.f);
+    }
+    for (int i = threadIdx.x; i < kMMK * b; i += blockDim.x) {
+      const int kk = i / b, c = i - kk * b;
+      const int gk = k0 + kk;
+      Xs32[i] = gk < ns ? Xg[(size_t)gk * b + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < MAXO; ++j) {
+      const int o = threadIdx.x + j * 256;
+      if (o < nout) {
+        const int r = o / b, c = o - r * b;
+        float2 a = acc[j];
+        for (int kk = 0; kk < kMMK; ++kk) cfma(a, Ps[r][kk], Xs32[kk * b + c]);
+        acc[j] = a;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < MAXO; ++j) {
+    const int o = threadIdx.x + j * 256;
+    if (o < nout) {
+      const int r = o / b, c = o - r * b;
+      if (r0 + r < ns) Yg[(size_t)(r0 + r) * b + c] = acc[j];
+    }
+  }
+}
+
+cudaError_t launch_eig_matmul32(const Geo& g, int b, const float2* P, const float2* X, float2* Y, cudaStream_t st) {
+  if (b > kEigMaxB) return cudaErrorInvalidValue;
+  const size_t sm = sizeof(float2) * (size_t)kMMK * b;
+  cudaFuncSetAttribute(k_eig_matmul32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  note_launches(1); k_eig_matmul32<<<dim3((g.ns + kMMRows - 1) / kMMRows, g.G), 256, sm, st>>>(g.ns, b, P, X, Y);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_eig_orth32(int ns, int b, float2* Y) {
+  extern __shared__ float2 osm32[];
+  float2* v = osm32;       // [ns]
+  float2* h = osm32 + ns;  // [b]
+  __shared__ double red[32];
+  __shared__ float nrm;
+  float2* Yg = Y + (size_t)blockIdx.x * ns * b;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = 0; c < b; ++c) {
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      for (int i = threadIdx.x; i < ns; i += blockDim.x)
+        v[i] = attempt == 0 ? Yg[(size_t)i * b + c] : make_float2(i == (c % ns) ? 1.f : 0.f, 0.f);
+      __syncthreads();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int j = wid; j < c; j += nw) {
+          float2 s = make_float2(0.f, 0.f);
+          for (int i = lane; i < ns; i += 32) cfmac(s, Yg[(size_t)i * b + j], v[i]);
+          s.x = warp_sumf(s.x);
+          s.y = warp_sumf(s.y);
+          if (lane == 0) h[j] = s;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+          float2 a = v[i];
+          for (int j = 0; j < c; ++j) {
+            const float2 q = Yg[(size_t)i * b + j];
+            const float2 hj = h[j];
+            a.x -= q.x * hj.x - q.y * hj.y;
+            a.y -= q.x * hj.y + q.y * hj.x;
+          }
+          v[i] = a;
+        }
+        __syncthreads();
+      }
+      double sq = 0.0;
+      for (int i = threadIdx.x; i < ns; i += blockDim.x) sq += (double)v[i].x * v[i].x + (double)v[i].y * v[i].y;
+      sq = block_sum(sq, red);
+      if (threadIdx.x == 0) nrm = (float)sqrt(sq);
+      __syncthreads();
+      if (nrm > 1e-30f) {
+        const float inv = 1.0f / nrm;
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) Yg[(size_t)i * b + c] = cscale(v[i], inv);
+        __syncthreads();
+        break;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+cudaError_t launch_eig_orth32(const Geo& g, int b, float2* Y, cudaStream_t st) {
+  const size_t sm = sizeof(float2) * (size_t)(g.ns + b);
+  cudaFuncSetAttribute(k_eig_orth32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  note_launches(1); k_eig_orth32<<<g.G, 256, sm, st>>>(g.ns, b, Y);
   return cudaGetLastError();
 }
 

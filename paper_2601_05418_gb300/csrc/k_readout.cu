@@ -90,18 +90,23 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
       const int row = row0 + r;
       const float2* crow = coil + n * L + (size_t)row * nx;
       const float2* xrow = x + (size_t)row * nx;
-      for (int i = threadIdx.x; i < g.ntx; i += blockDim.x) {
-        const int xx = i % nx;
-        A[spad(i)] = cmul(cmul(__ldg(crow + xx), ldm<P>(xrow + xx)), __ldg(g.pre + i));
+      // u = c_n x once per pixel, then its os pre-twiddled copies
+      for (int xx = threadIdx.x; xx < nx; xx += blockDim.x) {
+        const float2 u = cmul(__ldg(crow + xx), ldm<P>(xrow + xx));
+        for (int s = 0; s < os; ++s) A[spad(s * nx + xx)] = cmul(u, __ldg(g.pre + s * nx + xx));
       }
       __syncthreads();
       float2* R = fft_batch<-1, true>(A, B, os, nx, g.fx, tw, threadIdx.x, blockDim.x);
       float2* Ur = U + spad(r * st);
-      for (int i = threadIdx.x; i < g.ntx; i += blockDim.x) {
-        const int s = i / nx, m = i - s * nx;
-        const int t = m * os + s;
-        Ur[spad(t)] = cmul(R[spad(i)], post_at(g, t, row));
-      }
+      const float2* py = g.post_y + (size_t)(row % g.ny) * g.ntx;
+      const float2* pz = g.post_z + (size_t)(row / g.ny) * g.ntx;
+      for (int m = threadIdx.x; m < nx; m += blockDim.x)
+        for (int s = 0; s < os; ++s) {
+          const int t = m * os + s;
+          float2 pt = __ldg(py + t);
+          if (g.nz > 1) pt = cmul(pt, __ldg(pz + t));
+          Ur[spad(t)] = cmul(R[spad(s * nx + m)], pt);
+        }
       __syncthreads();
     }
     const int nw = n * w;

@@ -42,7 +42,8 @@ class Geom(C.Structure):
 
 
 class BuildParams(C.Structure):
-    _fields_ = [("eig_iters", C.c_int32), ("block", C.c_int32), ("keep_gram", C.c_int32)]
+    _fields_ = [("eig_iters", C.c_int32), ("block", C.c_int32), ("keep_gram", C.c_int32),
+                ("eig_iters_fp32", C.c_int32)]
 
 
 class GroupsInfo(C.Structure):
@@ -189,9 +190,10 @@ class Groups:
 
     @classmethod
     def build(cls, plan: Plan, coil: torch.Tensor, roi: torch.Tensor, T: Optional[np.ndarray] = None,
-              eig_iters: int = 0, block: int = 0, keep_gram: bool = False, stream=None) -> "Groups":
+              eig_iters: int = 0, block: int = 0, keep_gram: bool = False, eig_iters_fp32: int = 0,
+              stream=None) -> "Groups":
         h = _P()
-        bp = BuildParams(eig_iters, block, 1 if keep_gram else 0)
+        bp = BuildParams(eig_iters, block, 1 if keep_gram else 0, eig_iters_fp32)
         Tp = None
         if T is not None:
             Tc = np.ascontiguousarray(np.asarray(T, np.complex64))
