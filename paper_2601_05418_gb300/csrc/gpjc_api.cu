@@ -372,6 +372,9 @@ struct gpjc_groups {
   bool keep_gram;
   int b, iters, iters32, nblk, Kpad;
   float2 *P32, *X32, *Y32;  // FP32 phase of the subspace iteration
+  int2* tg_pairs;           // (128-row, 64-column) tile pairs of the tensor-core Gram
+  int tg_npairs;
+  bool tc_gram;             // tensor-core Gram (default) or the FFMA one
   // scratch kept for rebuilds, so a rebuild allocates nothing and does
   // not synchronise
   int *blockcount, *blockoff, *d_ref;
@@ -433,7 +436,11 @@ static gpjc_status groups_compute(gpjc_groups* gr, const float2* coil, const uin
   CK(launch_roi_compact(g, coil, roi, gr->blockoff, gr->pix, gr->nblk, st));
   CK(launch_roi_coils(g, coil, h_T ? gr->dT : nullptr, gr->pix, gr->dK, gr->Kpad, gr->chat, st));
   CK(cudaMemsetAsync(gr->P, 0, sizeof(double2) * (size_t)g.G * g.ns * g.ns, st));
-  CK(launch_gram(g, gr->chat, gr->pix, gr->dK, gr->Kpad, gr->d_ref, gr->P, st));
+  if (gr->tc_gram)
+    CK(launch_tc_gram(g, gr->chat, gr->pix, gr->dK, gr->Kpad, gr->d_ref, gr->tg_pairs, gr->tg_npairs, gr->P,
+                      gr->tc_status, st));
+  else
+    CK(launch_gram(g, gr->chat, gr->pix, gr->dK, gr->Kpad, gr->d_ref, gr->P, st));
   CK(launch_hermitize(g, gr->P, st));
   double2 *X = gr->X, *Y = gr->Y;
   CK(launch_eig_init(g, b, X, st));
@@ -532,6 +539,20 @@ extern "C" gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_c
       (s = m.alloc(&gr->Y32, nb)))
     return s;
   CK(cudaMemcpy(gr->d_ref, plan->ref.data(), sizeof(int) * g.G, cudaMemcpyHostToDevice));
+  {
+    const char* e = getenv("GPJC_SIMT_GRAM");
+    gr->tc_gram = !(e && e[0] == '1') && tc_gram_smem(g) <= 220 * 1024;
+    std::vector<int2> pairs;
+    for (int I = 0; I * 128 < g.ns; ++I)
+      for (int J = 0; J * 64 < g.ns; ++J)
+        if (J * 64 + 63 >= I * 128) pairs.push_back(make_int2(I, J));
+    gr->tg_npairs = (int)pairs.size();
+    if ((s = m.upload(&gr->tg_pairs, pairs))) return s;
+    if (!gr->tc_status) {
+      if ((s = m.alloc(&gr->tc_status, 1))) return s;
+      CK(cudaMemset(gr->tc_status, 0, sizeof(int)));
+    }
+  }
   if ((s = groups_compute(gr, (const float2*)d_coil, d_roi, h_T, st))) return s;
   // the ROI must not be empty: checked once here (later rebuilds are asynchronous)
   CK(cudaStreamSynchronize(st));

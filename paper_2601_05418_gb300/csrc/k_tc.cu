@@ -64,6 +64,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
     if (done) return true;
   }
 }
+// The same wait taken by every thread of the block, with a block-uniform
+// verdict (so that no thread leaves a loop whose barriers the others reach).
+// The parity is flipped only on success: after a timeout it still names the
+// operation in flight, which the block then drains before freeing TMEM.
+__device__ __forceinline__ bool block_wait(uint64_t* bar, uint32_t& parity) {
+  const bool ok = __syncthreads_and(mbar_wait(bar, parity) ? 1 : 0) != 0;
+  if (ok) parity ^= 1;
+  return ok;
+}
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
                                             uint64_t* bar) {
   asm volatile(
@@ -253,6 +262,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
   const uint32_t bbytes = (uint32_t)(t.npad * t.Kc * 2);
   uint32_t ph_ld = 0, ph_mma = 0;
   bool ok = true;
+  uint64_t* stuck = nullptr;
   const int m = tid;  // A row = output column (line l, occurrence q)
   const int l = m / t.n_occ, q = m - l * t.n_occ;
   for (int c = 0; c < t.nchunks && ok; ++c) {
@@ -261,9 +271,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
       tma_load_4d(stg, &tmap, x0, 0, c * t.ncc, l0, &bars[0]);
       bulk_g2s(Bt, Bpk + ((size_t)g * t.nchunks + c) * t.npad * t.Kc, bbytes, &bars[0]);
     }
-    ok = mbar_wait(&bars[0], ph_ld);
-    ph_ld ^= 1;
-    if (!ok) break;
+    if (!(ok = block_wait(&bars[0], ph_ld))) {
+      stuck = &bars[0];
+      break;
+    }
     // staging -> 16-bit core image (row m holds its column's samples of the chunk)
     for (int nl = 0; nl < t.ncc; ++nl) {
       const size_t base = ((size_t)(l * t.ncc + nl) * t.n_occ + q) * t.box0 + shift;
@@ -294,14 +305,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
       }
       mma_commit(&bars[1]);
     }
-    ok = mbar_wait(&bars[1], ph_mma);
-    ph_mma ^= 1;
+    if (!(ok = block_wait(&bars[1], ph_mma))) stuck = &bars[1];
   }
   if (!ok) {
     if (tid == 0) atomicExch(status, (int)kDevTimeout);
-    // drain whatever is still in flight before releasing the memory
-    mbar_wait(&bars[0], ph_ld);
-    mbar_wait(&bars[1], ph_mma);
+    // drain the operation still in flight before releasing the memory
+    mbar_wait(stuck, stuck == &bars[0] ? ph_ld : ph_mma);
   } else {
     tc_fence_after();
     // epilogue: lane m of TMEM holds column m; 8 fp32 columns = 4 complex values per load
@@ -376,6 +385,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
   const float s = t.scale[g];
   uint32_t ph_ld = 0, ph_mma = 0;
   bool ok = true;
+  uint64_t* stuck = nullptr;
   const int ntiles = (t.nexp + 255) / 256;
   for (int nt = 0; nt < ntiles && ok; ++nt) {
     const int nrows = min(256, t.nexp - nt * 256);  // multiple of 16
@@ -384,9 +394,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
       mbar_expect_tx(&bars[0], bbytes);
       bulk_g2s(Bt, Bpk + (size_t)g * t.nexp * t.Kx + (size_t)nt * 256 * t.Kx, bbytes, &bars[0]);
     }
-    ok = mbar_wait(&bars[0], ph_ld);
-    ph_ld ^= 1;
-    if (!ok) break;
+    if (!(ok = block_wait(&bars[0], ph_ld))) {
+      stuck = &bars[0];
+      break;
+    }
     if (tid == 0) {
       tc_fence_after();
       const uint32_t sbo = (uint32_t)(t.Kx / 8) * 128;
@@ -398,9 +409,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
       }
       mma_commit(&bars[1]);
     }
-    ok = mbar_wait(&bars[1], ph_mma);
-    ph_mma ^= 1;
-    if (!ok) break;
+    if (!(ok = block_wait(&bars[1], ph_mma))) {
+      stuck = &bars[1];
+      break;
+    }
     tc_fence_after();
     for (int col = 0; col < nrows; col += 8) {
       float v[8];
@@ -423,8 +435,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
   }
   if (!ok) {
     if (tid == 0) atomicExch(status, (int)kDevTimeout);
-    mbar_wait(&bars[0], ph_ld);
-    mbar_wait(&bars[1], ph_mma);
+    mbar_wait(stuck, stuck == &bars[0] ? ph_ld : ph_mma);
   }
   tc_fence_before();
   __syncthreads();
@@ -520,6 +531,183 @@ static cudaError_t launch_exp_t(const TcGeom& t, const float2* H, const uint16_t
 cudaError_t launch_tc_expand(const TcGeom& t, int fmt, const float2* H, const uint16_t* Bx, float2* V, int rows,
                              int* status, cudaStream_t st) {
   return fmt == 1 ? launch_exp_t<1>(t, H, Bx, V, rows, status, st) : launch_exp_t<0>(t, H, Bx, V, rows, status, st);
+}
+
+}  // namespace gpjc
+
+// ====================================================================== Gram --
+// P_g = sum_r v_r v_r^H on the tensor cores (Eq. 9-11).  v is generated per
+// pixel chunk from the normalised coil values and the patch phases, scaled
+// by 2^12 and split into an FP16 head and remainder; three MMAs per K step
+// (head x head, head x rest, rest x head) keep the products at about FP32
+// accuracy.  Real embedding: A rows are i (128 per tile), K = (pixel, re/im),
+// B rows are (j, part) with part 0 = [Re v_j, Im v_j], part 1 = [-Im v_j, Re v_j],
+// so D[i][2 j' + 0] = Re P_ij and D[i][2 j' + 1] = Im P_ij.  The TMEM
+// accumulator (FP32) is drained into FP64 shared-memory sums every
+// kTgRun chunks; slabs of pixels are combined with FP64 atomics.
+namespace gpjc {
+
+constexpr int kTgKC = 32;      // pixels per chunk (K = 64)
+constexpr int kTgRun = 8;      // chunks per FP32 run (256 pixels)
+constexpr int kTgSlab = 4096;  // pixels per block
+constexpr float kTgScale = 4096.0f;  // 2^12 before the split; products carry 2^24
+
+__device__ __forceinline__ void split_f16(float a, float b, uint32_t* hi, uint32_t* lo) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+  *hi = *reinterpret_cast<const uint32_t*>(&h);
+  *lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gram(Geo g, const float2* __restrict__ chat,
+                                                          const int* __restrict__ pix,
+                                                          const int* __restrict__ dK, int Kpad,
+                                                          const int* __restrict__ pref,
+                                                          const int2* __restrict__ pairs,
+                                                          double2* __restrict__ P, int* status) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  double* acc64 = (double*)tsm;                         // [column][row], 128 x 128
+  uint16_t* Ah = (uint16_t*)(acc64 + 128 * 128);        // 128 x 64 images
+  uint16_t* Al = Ah + 128 * 64;
+  uint16_t* Bh = Al + 128 * 64;
+  uint16_t* Bl = Bh + 128 * 64;
+  float2* psi = (float2*)(Bl + 128 * 64);               // [w][kTgKC]
+  uint64_t* bar = (uint64_t*)(psi + g.w * kTgKC);
+  uint32_t* tmem_slot = (uint32_t*)(bar + 1);
+  const int grp = blockIdx.y;
+  const int2 pr = pairs[blockIdx.x];
+  const int i0 = pr.x * 128, j0 = pr.y * 64;
+  const int K = *dK;
+  const int kend_all = ((K + kTgKC - 1) / kTgKC) * kTgKC;
+  const int k_begin = blockIdx.z * kTgSlab;
+  const int k_end = min(kend_all, k_begin + kTgSlab);
+  if (k_begin >= k_end) return;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(tmem_slot, 128);
+  for (int i = tid; i < 128 * 128; i += kTcThreads) acc64[i] = 0.0;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = idesc_f16(0, 128);
+  const uint32_t sbo = (64 / 8) * 128;
+  const int t0 = pref[grp] * g.w;
+  const float inv_ny = 1.0f / (float)g.ny, inv_nz = 1.0f / (float)g.nz;
+  // this thread's A row i and B row (j, part)
+  const int ia = i0 + tid;
+  const int na = ia / g.w, taua = ia - na * g.w;
+  const int jb = j0 + (tid >> 1), part = tid & 1;
+  const int nb = jb / g.w, taub = jb - nb * g.w;
+  uint32_t phase = 0;
+  bool ok = true;
+  int run = 0;
+  for (int k0 = k_begin; k0 < k_end && ok; k0 += kTgKC) {
+    for (int idx = tid; idx < g.w * kTgKC; idx += kTcThreads) {
+      const int tau = idx / kTgKC, r = idx - tau * kTgKC;
+      const int k = k0 + r;
+      float2 e = make_float2(0.f, 0.f);
+      if (k < K) {
+        const int p = pix[k];
+        const int x = p % g.nx, row = p / g.nx;
+        const int y = row % g.ny, z = row / g.ny;
+        const int t = t0 + tau;
+        int prod = ((t - g.ntx / 2) * (x - g.nx / 2)) % g.ntx;
+        if (prod < 0) prod += g.ntx;
+        const float wave = g.ay[t] * (float)(y - g.ny / 2) * inv_ny +
+                           (g.nz > 1 ? g.az[t] * (float)(z - g.nz / 2) * inv_nz : 0.0f);
+        e = expipi(-(2.0f * (float)prod / (float)g.ntx + 2.0f * wave));
+      }
+      psi[idx] = e;
+    }
+    __syncthreads();
+    for (int r = 0; r < kTgKC; ++r) {
+      float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
+      if (ia < g.ns) va = cscale(cmul(chat[(size_t)na * Kpad + k0 + r], psi[taua * kTgKC + r]), kTgScale);
+      if (jb < g.ns) vb = cscale(cmul(chat[(size_t)nb * Kpad + k0 + r], psi[taub * kTgKC + r]), kTgScale);
+      uint32_t h, l;
+      split_f16(va.x, va.y, &h, &l);
+      *(uint32_t*)(Ah + core_off(tid, 2 * r, 64)) = h;
+      *(uint32_t*)(Al + core_off(tid, 2 * r, 64)) = l;
+      if (part == 0)
+        split_f16(vb.x, vb.y, &h, &l);
+      else
+        split_f16(-vb.y, vb.x, &h, &l);
+      *(uint32_t*)(Bh + core_off(tid, 2 * r, 64)) = h;
+      *(uint32_t*)(Bl + core_off(tid, 2 * r, 64)) = l;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint64_t ah = umma_desc(Ah + ks * 128, 128, sbo), al = umma_desc(Al + ks * 128, 128, sbo);
+        const uint64_t bh = umma_desc(Bh + ks * 128, 128, sbo), bl = umma_desc(Bl + ks * 128, 128, sbo);
+        mma_f16(tmem, ah, bh, idesc, (run > 0 || ks > 0) ? 1u : 0u);
+        mma_f16(tmem, ah, bl, idesc, 1u);
+        mma_f16(tmem, al, bh, idesc, 1u);
+      }
+      mma_commit(bar);
+    }
+    if (!(ok = block_wait(bar, phase))) break;
+    if (++run == kTgRun || k0 + kTgKC >= k_end) {
+      run = 0;
+      tc_fence_after();
+      // drain: lane tid holds row i0 + tid, 128 FP32 columns
+      for (int col = 0; col < 128; col += 8) {
+        float v[8];
+        tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc64[(col + q) * 128 + tid] += (double)v[q];
+      }
+      tc_fence_before();
+    }
+    __syncthreads();
+  }
+  if (!ok) {
+    if (tid == 0) atomicExch(status, (int)kDevTimeout);
+    mbar_wait(bar, phase);
+  } else {
+    const double s = 1.0 / ((double)kTgScale * (double)kTgScale);
+    double2* Pg = P + (size_t)grp * g.ns * g.ns;
+    const int i = i0 + tid;
+    if (i < g.ns)
+      for (int jj = 0; jj < 64; ++jj) {
+        const int j = j0 + jj;
+        if (j < g.ns && i <= j) {
+          double2* d = Pg + (size_t)i * g.ns + j;
+          atomicAdd(&d->x, acc64[(2 * jj) * 128 + tid] * s);
+          atomicAdd(&d->y, acc64[(2 * jj + 1) * 128 + tid] * s);
+        }
+      }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, 128);
+}
+
+size_t tc_gram_smem(const Geo& g) {
+  return sizeof(double) * 128 * 128 + 4 * 128 * 64 * 2 + sizeof(float2) * (size_t)g.w * kTgKC + 64;
+}
+
+cudaError_t launch_tc_gram(const Geo& g, const float2* chat, const int* pix, const int* dK, int Kpad,
+                           const int* pref, const int2* pairs, int npairs, double2* P, int* status,
+                           cudaStream_t st) {
+  const size_t sm = tc_gram_smem(g);
+  static size_t attr = 0;
+  if (sm > attr) {
+    cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr = sm;
+  }
+  const int nslab = (Kpad + kTgSlab - 1) / kTgSlab;
+  note_launches(1); k_tc_gram<<<dim3(npairs, g.G, nslab), kTcThreads, sm, st>>>(g, chat, pix, dK, Kpad, pref, pairs,
+                                                                               P, status);
+  return cudaGetLastError();
 }
 
 }  // namespace gpjc

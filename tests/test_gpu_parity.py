@@ -198,8 +198,13 @@ def test_compress_matches_oracle(gp, name):
 
 # ------------------------------------------------------------ groups --
 
+@pytest.mark.parametrize("simt", [False, True])
 @pytest.mark.parametrize("name", ["2d128", "ragged", "3d56"])
-def test_gram_matches_oracle(gp, name):
+def test_gram_matches_oracle(gp, name, simt, monkeypatch):
+    """Both Gram kernels: the tensor-core one (FP16 head/remainder split) and
+    the FFMA one (GPJC_SIMT_GRAM=1)."""
+    if simt:
+        monkeypatch.setenv("GPJC_SIMT_GRAM", "1")
     g = geometries()[name]
     coils, rho, roi = case_for(g, 16)
     plan = gp.Plan(g)
