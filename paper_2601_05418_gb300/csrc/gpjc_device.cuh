@@ -142,17 +142,6 @@ __host__ __device__ constexpr int spad_size(int n) { return n + (n >> 3) + 1; }
 // One Stockham stage of radix R on `batch` contiguous transforms of length n.
 // tw[k] = exp(-2 pi i k / n) for k < n.  With PAD, element i of the logical
 // buffer lives at spad(i).
-// floor(a / d) for 0 <= a < 2^16 and 1 <= d < 2^16 by one wide multiply
-// with magic = ceil(2^32 / d) (a 33-bit value for d = 1, hence 64-bit): the
-// rounding error of the magic adds less than a 2^-16 <= 1/d to a / d, so
-// the quotient never crosses an integer.
-__device__ __forceinline__ unsigned long long fdiv_magic(unsigned d) {
-  return (0x100000000ull + d - 1) / d;
-}
-__device__ __forceinline__ int fdiv(int a, unsigned long long magic) {
-  return (int)(((unsigned long long)(unsigned)a * magic) >> 32);
-}
-
 template <int R, int SIGN, bool PAD = false>
 __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, float2* __restrict__ dst,
                                                int n, int batch, int bs, int ns,
@@ -160,13 +149,12 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
   const int m = n / R;
   const int total = batch * m;
   const int twstep = n / (ns * R);
-  const unsigned long long mg_m = fdiv_magic((unsigned)m), mg_ns = fdiv_magic((unsigned)ns);
   for (int idx = tid; idx < total; idx += nthr) {
-    const int f = fdiv(idx, mg_m);
+    const int f = idx / m;
     const int j = idx - f * m;
     const int sb = f * bs;
     float2 v[R];
-    const int jq = fdiv(j, mg_ns);
+    const int jq = j / ns;
     const int k = j - jq * ns;
 #pragma unroll
     for (int r = 0; r < R; ++r) {

@@ -171,7 +171,6 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
   for (int i = threadIdx.x; i < g.nx; i += blockDim.x) tw[i] = g.tw_x[i];
   const size_t L = (size_t)g.rows * g.nx;
   const int nx = g.nx, os = g.os, w = g.w, ns = g.ns;
-  const unsigned long long mg_os = fdiv_magic((unsigned)os);
 
   float2 xacc[MAXX];
 #pragma unroll
@@ -221,7 +220,7 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
         for (int tt = 0; tt < 4; ++tt) {
           if (tt >= h.z) continue;
           const int t = t0 + tt;
-          const int mm = fdiv(t, mg_os), s = t - mm * os;
+          const int mm = t / os, s = t - mm * os;
           float2 pt = __ldg(py + t);
           if (g.nz > 1) pt = cmul(pt, __ldg(pz + t));
           Ur[spad(s * nx + mm)] = cmulc(pt, acc[c][tt]);
