@@ -516,8 +516,11 @@ extern "C" gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_c
   std::unique_ptr<gpjc_groups> guard(gr);
   gr->plan = plan;
   gr->b = b;
-  gr->iters = bp.eig_iters > 0 ? bp.eig_iters : 3;
   gr->iters32 = bp.eig_iters_fp32 > 0 ? bp.eig_iters_fp32 : (bp.eig_iters_fp32 < 0 ? 0 : 10);
+  // after the FP32 phase one FP64 iteration reaches FP64 accuracy (its
+  // subspace error is already at the FP32 rounding level); without it the
+  // FP64 iteration starts from random vectors
+  gr->iters = bp.eig_iters > 0 ? bp.eig_iters : (gr->iters32 > 0 ? 1 : 12);
   gr->keep_gram = bp.keep_gram != 0;
   gr->built = true;
   gr->host_valid = false;
@@ -679,7 +682,8 @@ struct gpjc_op {
   const gpjc_plan* plan;
   const float2* coil;
   gpjc_precision prec;
-  int nchunk, nchunk_max;
+  int nchunk, nchunk_max;      // coil chunks of the forward readout (partial Hpart planes)
+  int nchunk_a, nchunk_a_max;  // coil chunks of the adjoint readout (partial images in xparts)
   size_t L;
   float2 *Hpart, *T, *H2, *xparts;
   float2 *vb, *vr, *vp, *vy, *vv, *vtmp;
@@ -726,6 +730,17 @@ static void prof_end(gpjc_op* op, cudaStream_t st, size_t mark) {
     cudaEventRecordWithFlags(op->prof_pool[mark + 1], st, g_capturing ? cudaEventRecordExternal : 0);
 }
 
+// adjoint readout: enough (row block, coil chunk) blocks for three
+// resident blocks on each of the 152 SMs
+static int auto_nchunk_adj(const gpjc_plan* p) {
+  const int rows = p->ny * p->nz;
+  const int rb = p->rt_a.rb ? p->rt_a.rb : 1;
+  const int blocks = (rows + rb - 1) / rb;
+  int n = 1;
+  while (blocks * n < 3 * 152 && n * 2 <= p->nc) n *= 2;
+  return n;
+}
+
 static int auto_nchunk(const gpjc_plan* p) {
   const int rows = p->ny * p->nz;
   int n = 1;
@@ -762,11 +777,18 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   op->nchunk_max = nmax;
   const Geo& g = p->geo;
   op->L = (size_t)g.rows * g.nx;
+  // the adjoint's partial images are small: allow up to nc chunks (1 GB cap)
+  {
+    int n = 1;
+    while (n * 2 <= p->nc && (size_t)n * 2 * op->L * sizeof(float2) <= ((size_t)1 << 30)) n *= 2;
+    op->nchunk_a_max = std::max(n, nmax);
+    op->nchunk_a = std::min(auto_nchunk_adj(p), op->nchunk_a_max);
+  }
   const size_t HN = (size_t)g.rows * g.ntxc;
   gpjc_status s;
   DevMem& m = op->mem;
   if ((s = m.alloc(&op->Hpart, HN * nmax)) || (s = m.alloc(&op->H2, HN)) ||
-      (s = m.alloc(&op->xparts, op->L * nmax)) || (s = m.alloc(&op->vb, op->L)) ||
+      (s = m.alloc(&op->xparts, op->L * (size_t)op->nchunk_a_max)) || (s = m.alloc(&op->vb, op->L)) ||
       (s = m.alloc(&op->vr, op->L)) || (s = m.alloc(&op->vp, op->L)) || (s = m.alloc(&op->vy, op->L)) ||
       (s = m.alloc(&op->vv, op->L)) || (s = m.alloc(&op->vtmp, op->L)))
     return s;
@@ -848,11 +870,11 @@ static cudaError_t readout_adj(const gpjc_op* op, cudaStream_t st) {
     cudaError_t e =
         launch_tc_expand(t, fmt, op->H2, op->gr->tc_bx[fmt], (float2*)op->V16, p->geo.rows, op->status, st);
     if (e != cudaSuccess) return e;
-    return launch_sim_adj(p->geo, (const float2*)op->V16, op->coil, op->xparts, op->nchunk, st);
+    return launch_sim_adj(p->geo, (const float2*)op->V16, op->coil, op->xparts, op->nchunk_a, st);
   }
   if (p->rt_a.rb && !op->legacy_readout)
-    return launch_k1a_tiled(p->geo, p->rt_a, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st);
-  return launch_k1_adj_fp32(p->geo, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk, st);
+    return launch_k1a_tiled(p->geo, p->rt_a, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk_a, st);
+  return launch_k1_adj_fp32(p->geo, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk_a, st);
 }
 
 static gpjc_status op_fwd(const gpjc_op* cop, const float2* x, float2* y, cudaStream_t st) {
@@ -909,7 +931,7 @@ extern "C" gpjc_status gpjc_apply_EH(const gpjc_op* op, const float* d_y, float*
   cudaStream_t st = (cudaStream_t)stream;
   gpjc_status s = op_adj_parts(op, (const float2*)d_y, st);
   if (s) return s;
-  CK(launch_sum_parts(op->xparts, op->nchunk, op->L, (float2*)d_x, nullptr, nullptr, nullptr, st));
+  CK(launch_sum_parts(op->xparts, op->nchunk_a, op->L, (float2*)d_x, nullptr, nullptr, nullptr, st));
   return GPJC_OK;
 }
 
@@ -919,7 +941,7 @@ extern "C" gpjc_status gpjc_apply_normal(const gpjc_op* op, const float* d_x, fl
   cudaStream_t st = (cudaStream_t)stream;
   gpjc_status s = op_normal_parts(op, (const float2*)d_x, d_qq, st);
   if (s) return s;
-  CK(launch_sum_parts(op->xparts, op->nchunk, op->L, (float2*)d_out, nullptr, nullptr, nullptr, st));
+  CK(launch_sum_parts(op->xparts, op->nchunk_a, op->L, (float2*)d_out, nullptr, nullptr, nullptr, st));
   return GPJC_OK;
 }
 
@@ -952,8 +974,30 @@ extern "C" gpjc_status gpjc_simulate_adjoint(const gpjc_op* cop, const float* d_
   const Geo& g = op->plan->geo;
   cudaStream_t st = (cudaStream_t)stream;
   CK(launch_pe_adj(g, (const float2*)d_S, g.nc * g.ntx, op->TV, op->V, st));
-  CK(launch_sim_adj(g, op->V, op->coil, op->xparts, op->nchunk, st));
-  CK(launch_sum_parts(op->xparts, op->nchunk, op->L, (float2*)d_x, nullptr, nullptr, nullptr, st));
+  CK(launch_sim_adj(g, op->V, op->coil, op->xparts, op->nchunk_a, st));
+  CK(launch_sum_parts(op->xparts, op->nchunk_a, op->L, (float2*)d_x, nullptr, nullptr, nullptr, st));
+  return GPJC_OK;
+}
+
+// times one application of E_c^H E_c (both readout stages, the phase-encode
+// stage and the sum of the partial images) with the current chunk counts
+// (best of three runs of five applications, after one warm-up application)
+static gpjc_status time_normal(gpjc_op* op, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+  gpjc_status s;
+  *ms = 1e30f;
+  for (int trial = 0; trial < 4; ++trial) {
+    if (trial > 0) CK(cudaEventRecord(e0, st));
+    for (int r = 0; r < (trial > 0 ? 5 : 1); ++r) {
+      if ((s = op_normal_parts(op, op->vv, nullptr, st))) return s;
+      CK(launch_sum_parts(op->xparts, op->nchunk_a, op->L, op->vtmp, nullptr, nullptr, nullptr, st));
+    }
+    if (trial == 0) continue;
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    *ms = std::min(*ms, t);
+  }
   return GPJC_OK;
 }
 
@@ -963,36 +1007,38 @@ extern "C" gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchu
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int keep = op->nchunk;
-  float best = 1e30f;
-  int best_n = keep;
-  for (int n = 1; n <= op->nchunk_max; n *= 2) {
-    op->nchunk = n;
-    gpjc_status s = op_normal_parts(op, op->vv, nullptr, st);  // warm-up
-    if (s) {
-      op->nchunk = keep;
-      return s;
+  const int keep_f = op->nchunk, keep_a = op->nchunk_a;
+  gpjc_status s = GPJC_OK;
+  // adjoint chunks first (forward fixed), then forward chunks
+  for (int pass = 0; pass < 2 && !s; ++pass) {
+    int* knob = pass == 0 ? &op->nchunk_a : &op->nchunk;
+    const int nmax = pass == 0 ? op->nchunk_a_max : op->nchunk_max;
+    float best = 1e30f;
+    int best_n = *knob;
+    for (int n = 1; n <= nmax && !s; n *= 2) {
+      *knob = n;
+      float ms = 0.f;
+      if ((s = time_normal(op, st, e0, e1, &ms))) break;
+      if (ms < best) {
+        best = ms;
+        best_n = n;
+      }
     }
-    CK(cudaEventRecord(e0, st));
-    for (int r = 0; r < 5; ++r) op_normal_parts(op, op->vv, nullptr, st);
-    CK(cudaEventRecord(e1, st));
-    CK(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
-      best_n = n;
-    }
+    *knob = best_n;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  op->nchunk = best_n;
+  if (s) {
+    op->nchunk = keep_f;
+    op->nchunk_a = keep_a;
+    return s;
+  }
   if (op->gexec) {
     cudaGraphExecDestroy(op->gexec);
     op->gexec = nullptr;
     op->gkey.clear();
   }
-  if (nchunk_out) *nchunk_out = best_n;
+  if (nchunk_out) *nchunk_out = op->nchunk;
   return GPJC_OK;
 }
 
@@ -1008,11 +1054,11 @@ static gpjc_status recon_body(gpjc_op* op, const float2* Sc, float2* x, const gp
   CK(cudaMemsetAsync(op->status, 0, sizeof(int), st));
   // b = E_c^H S'
   if ((s = op_adj_parts(op, Sc, st))) return s;
-  CK(launch_sum_parts(op->xparts, op->nchunk, L, op->vb, op->partials, op->counter, sc + SC_BB, st));
+  CK(launch_sum_parts(op->xparts, op->nchunk_a, L, op->vb, op->partials, op->counter, sc + SC_BB, st));
   if (rp.alg == GPJC_CG) {
     if (rp.use_x0) {
       if ((s = op_normal_parts(op, x, nullptr, st))) return s;
-      CK(launch_sum_parts(op->xparts, op->nchunk, L, op->vtmp, nullptr, nullptr, nullptr, st));
+      CK(launch_sum_parts(op->xparts, op->nchunk_a, L, op->vtmp, nullptr, nullptr, nullptr, st));
       CK(launch_axpby(op->vr, op->vb, op->vtmp, 1.0f, -1.0f, L, st));
     } else {
       CK(launch_zero(x, L, st));
@@ -1025,7 +1071,7 @@ static gpjc_status recon_body(gpjc_op* op, const float2* Sc, float2* x, const gp
       double* rrn = sc + (it % 2 ? SC_RR0 : SC_RR1);
       if ((s = op_normal_parts(op, op->vp, sc + SC_QQ, st))) return s;
       double* h = (it + 1 < op->hist_len) ? op->hist + it + 1 : nullptr;
-      CK(launch_cg_update1(op->xparts, op->nchunk, L, x, op->vr, op->vp, rr, sc + SC_QQ, op->partials, op->counter,
+      CK(launch_cg_update1(op->xparts, op->nchunk_a, L, x, op->vr, op->vp, rr, sc + SC_QQ, op->partials, op->counter,
                            rrn, h, op->status, st));
       CK(launch_cg_update2(op->vp, op->vr, L, rr, rrn, st));
     }
@@ -1039,7 +1085,7 @@ static gpjc_status recon_body(gpjc_op* op, const float2* Sc, float2* x, const gp
     CK(launch_scale_by(op->vv, op->vb, sc + SC_BB, L, nullptr, st));
     for (int it = 0; it < pit; ++it) {
       if ((s = op_normal_parts(op, op->vv, nullptr, st))) return s;
-      CK(launch_sum_parts(op->xparts, op->nchunk, L, op->vtmp, op->partials, op->counter, sc + SC_NV, st));
+      CK(launch_sum_parts(op->xparts, op->nchunk_a, L, op->vtmp, op->partials, op->counter, sc + SC_NV, st));
       CK(launch_scale_by(op->vv, op->vtmp, sc + SC_NV, L, sc + SC_LIP, st));
     }
   }
@@ -1050,7 +1096,7 @@ static gpjc_status recon_body(gpjc_op* op, const float2* Sc, float2* x, const gp
     if ((s = op_normal_parts(op, op->vy, nullptr, st))) return s;
     const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
     const double ck = (t - 1.0) / tn;
-    CK(launch_fista_step(g, op->xparts, op->nchunk, x, op->vy, op->vb, sc + SC_LIP, rp.lambda, rp.haar_levels, ck,
+    CK(launch_fista_step(g, op->xparts, op->nchunk_a, x, op->vy, op->vb, sc + SC_LIP, rp.lambda, rp.haar_levels, ck,
                          op->status, st));
     t = tn;
   }
@@ -1075,11 +1121,12 @@ extern "C" gpjc_status gpjc_recon(const gpjc_op* cop, const float* d_Sc, float* 
   cudaStream_t st = (cudaStream_t)stream;
   gpjc_status s;
   if (rp.use_graph) {
-    std::vector<char> key(sizeof(rp) + 2 * sizeof(void*) + sizeof(int));
+    std::vector<char> key(sizeof(rp) + 2 * sizeof(void*) + 2 * sizeof(int));
     memcpy(key.data(), &rp, sizeof(rp));
     memcpy(key.data() + sizeof(rp), &d_Sc, sizeof(void*));
     memcpy(key.data() + sizeof(rp) + sizeof(void*), &d_x, sizeof(void*));
     memcpy(key.data() + sizeof(rp) + 2 * sizeof(void*), &op->nchunk, sizeof(int));
+    memcpy(key.data() + sizeof(rp) + 2 * sizeof(void*) + sizeof(int), &op->nchunk_a, sizeof(int));
     cudaStream_t cs = op->cap_st;
     CK(cudaEventRecord(op->ev_in, st));
     CK(cudaStreamWaitEvent(cs, op->ev_in, 0));

@@ -605,33 +605,55 @@ cudaError_t launch_eig_matmul32(const Geo& g, int b, const float2* P, const floa
   return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(256) k_eig_orth32(int ns, int b, float2* Y) {
-  extern __shared__ float2 osm32[];
-  float2* v = osm32;       // [ns]
-  float2* h = osm32 + ns;  // [b]
+// Orthonormalise the columns of Y[g] (ns x b, row-major) in place: classical
+// Gram-Schmidt with one re-orthogonalisation pass per column (CGS2), a
+// column that vanishes is replaced by a unit vector.  One block per group;
+// when the group's block fits in shared memory (SM) all passes run there.
+// C is float2 (FP32 phase) or double2; norms are accumulated in double.
+__device__ __forceinline__ void cacc_conj(float2& s, float2 a, float2 b) { cfmac(s, a, b); }
+__device__ __forceinline__ void cacc_conj(double2& s, double2 a, double2 b) { zfmac(s, a, b); }
+__device__ __forceinline__ float2 cmk(double re, double im, float2*) { return make_float2((float)re, (float)im); }
+__device__ __forceinline__ double2 cmk(double re, double im, double2*) { return make_double2(re, im); }
+__device__ __forceinline__ float wsum(float v) { return warp_sumf(v); }
+__device__ __forceinline__ double wsum(double v) { return warp_sum(v); }
+
+template <typename C, bool SM>
+__global__ void __launch_bounds__(256) k_eig_orth_t(int ns, int b, C* Y) {
+  extern __shared__ __align__(16) unsigned char orth_sm[];
+  C* v = (C*)orth_sm;  // [ns]
+  C* h = v + ns;       // [b]
+  C* Ys = h + b;       // [ns][b + 1] when SM (odd row stride: no bank conflicts down a column)
   __shared__ double red[32];
-  __shared__ float nrm;
-  float2* Yg = Y + (size_t)blockIdx.x * ns * b;
+  __shared__ double nrm;
+  C* Yg = Y + (size_t)blockIdx.x * ns * b;
+  C* Yw = SM ? Ys : Yg;
+  const int ld = SM ? b + 1 : b;
+  if (SM) {
+    for (int i = threadIdx.x; i < ns * b; i += blockDim.x) Ys[(i / b) * ld + i % b] = Yg[i];
+    __syncthreads();
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int c = 0; c < b; ++c) {
     for (int attempt = 0; attempt < 2; ++attempt) {
       for (int i = threadIdx.x; i < ns; i += blockDim.x)
-        v[i] = attempt == 0 ? Yg[(size_t)i * b + c] : make_float2(i == (c % ns) ? 1.f : 0.f, 0.f);
+        v[i] = attempt == 0 ? Yw[(size_t)i * ld + c] : cmk(i == (c % ns) ? 1.0 : 0.0, 0.0, (C*)nullptr);
       __syncthreads();
       for (int pass = 0; pass < 2; ++pass) {
+        // h_j = <y_j, v> for the c finished columns (one warp per column)
         for (int j = wid; j < c; j += nw) {
-          float2 s = make_float2(0.f, 0.f);
-          for (int i = lane; i < ns; i += 32) cfmac(s, Yg[(size_t)i * b + j], v[i]);
-          s.x = warp_sumf(s.x);
-          s.y = warp_sumf(s.y);
-          if (lane == 0) h[j] = s;
+          C sacc = cmk(0.0, 0.0, (C*)nullptr);
+          for (int i = lane; i < ns; i += 32) cacc_conj(sacc, Yw[(size_t)i * ld + j], v[i]);
+          sacc.x = wsum(sacc.x);
+          sacc.y = wsum(sacc.y);
+          if (lane == 0) h[j] = sacc;
         }
         __syncthreads();
+        // v -= Y_{<c} h
         for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-          float2 a = v[i];
+          C a = v[i];
+          const C* yr = Yw + (size_t)i * ld;
           for (int j = 0; j < c; ++j) {
-            const float2 q = Yg[(size_t)i * b + j];
-            const float2 hj = h[j];
+            const C q = yr[j], hj = h[j];
             a.x -= q.x * hj.x - q.y * hj.y;
             a.y -= q.x * hj.y + q.y * hj.x;
           }
@@ -642,88 +664,40 @@ __global__ void __launch_bounds__(256) k_eig_orth32(int ns, int b, float2* Y) {
       double sq = 0.0;
       for (int i = threadIdx.x; i < ns; i += blockDim.x) sq += (double)v[i].x * v[i].x + (double)v[i].y * v[i].y;
       sq = block_sum(sq, red);
-      if (threadIdx.x == 0) nrm = (float)sqrt(sq);
+      if (threadIdx.x == 0) nrm = sqrt(sq);
       __syncthreads();
-      if (nrm > 1e-30f) {
-        const float inv = 1.0f / nrm;
-        for (int i = threadIdx.x; i < ns; i += blockDim.x) Yg[(size_t)i * b + c] = cscale(v[i], inv);
+      const double nv = nrm;
+      if (nv > (sizeof(C) == sizeof(float2) ? 1e-30 : 1e-280)) {
+        const double inv = 1.0 / nv;
+        for (int i = threadIdx.x; i < ns; i += blockDim.x)
+          Yw[(size_t)i * ld + c] = cmk(v[i].x * inv, v[i].y * inv, (C*)nullptr);
         __syncthreads();
         break;
       }
       __syncthreads();
     }
   }
-}
-
-cudaError_t launch_eig_orth32(const Geo& g, int b, float2* Y, cudaStream_t st) {
-  const size_t sm = sizeof(float2) * (size_t)(g.ns + b);
-  cudaFuncSetAttribute(k_eig_orth32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  note_launches(1); k_eig_orth32<<<g.G, 256, sm, st>>>(g.ns, b, Y);
-  return cudaGetLastError();
-}
-
-// Orthonormalise the columns of Y[g] (ns x b) in place: classical
-// Gram-Schmidt with one re-orthogonalisation pass per column.
-__global__ void __launch_bounds__(256) k_eig_orth(int ns, int b, double2* Y) {
-  extern __shared__ double2 osm[];
-  double2* v = osm;       // [ns]
-  double2* h = osm + ns;  // [b]
-  __shared__ double red[32];
-  double2* Yg = Y + (size_t)blockIdx.x * ns * b;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int c = 0; c < b; ++c) {
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-        if (attempt == 0)
-          v[i] = Yg[(size_t)i * b + c];
-        else
-          v[i] = make_double2(i == (c % ns) ? 1.0 : 0.0, 0.0);
-      }
-      __syncthreads();
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int j = wid; j < c; j += nw) {
-          double2 s = make_double2(0.0, 0.0);
-          for (int i = lane; i < ns; i += 32) zfmac(s, Yg[(size_t)i * b + j], v[i]);
-          s.x = warp_sum(s.x);
-          s.y = warp_sum(s.y);
-          if (lane == 0) h[j] = s;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-          double2 a = v[i];
-          for (int j = 0; j < c; ++j) {
-            const double2 q = Yg[(size_t)i * b + j];
-            const double2 hj = h[j];
-            a.x -= q.x * hj.x - q.y * hj.y;
-            a.y -= q.x * hj.y + q.y * hj.x;
-          }
-          v[i] = a;
-        }
-        __syncthreads();
-      }
-      double s = 0.0;
-      for (int i = threadIdx.x; i < ns; i += blockDim.x) s += v[i].x * v[i].x + v[i].y * v[i].y;
-      s = block_sum(s, red);
-      __shared__ double nrm;
-      if (threadIdx.x == 0) nrm = sqrt(s);
-      __syncthreads();
-      if (nrm > 1e-280) {
-        const double inv = 1.0 / nrm;
-        for (int i = threadIdx.x; i < ns; i += blockDim.x) Yg[(size_t)i * b + c] = zscale(v[i], inv);
-        __syncthreads();
-        break;
-      }
-      __syncthreads();
-    }
+  if (SM) {
+    for (int i = threadIdx.x; i < ns * b; i += blockDim.x) Yg[i] = Ys[(i / b) * ld + i % b];
   }
 }
 
-cudaError_t launch_eig_orth(const Geo& g, int b, double2* Y, cudaStream_t st) {
-  const size_t sm = sizeof(double2) * (size_t)(g.ns + b);
-  cudaFuncSetAttribute(k_eig_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  note_launches(1); k_eig_orth<<<g.G, 256, sm, st>>>(g.ns, b, Y);
+template <typename C>
+static cudaError_t launch_orth_t(const Geo& g, int b, C* Y, cudaStream_t st) {
+  const size_t base = sizeof(C) * (size_t)(g.ns + b);
+  const size_t full = base + sizeof(C) * (size_t)g.ns * (b + 1);
+  if (full <= 200 * 1024) {
+    cudaFuncSetAttribute(k_eig_orth_t<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)full);
+    note_launches(1); k_eig_orth_t<C, true><<<g.G, 256, full, st>>>(g.ns, b, Y);
+  } else {
+    cudaFuncSetAttribute(k_eig_orth_t<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base);
+    note_launches(1); k_eig_orth_t<C, false><<<g.G, 256, base, st>>>(g.ns, b, Y);
+  }
   return cudaGetLastError();
 }
+
+cudaError_t launch_eig_orth32(const Geo& g, int b, float2* Y, cudaStream_t st) { return launch_orth_t(g, b, Y, st); }
+cudaError_t launch_eig_orth(const Geo& g, int b, double2* Y, cudaStream_t st) { return launch_orth_t(g, b, Y, st); }
 
 // Hm[g][a][c] = sum_i conj(Q[i][a]) Z[i][c]
 __global__ void k_eig_project(int ns, int b, const double2* __restrict__ Q, const double2* __restrict__ Z,
