@@ -108,6 +108,7 @@ struct DevMem {
 bool factor_fft(int n, FftPlan* pl) {
   pl->n = n;
   pl->nst = 0;
+  pl->n1 = pl->n2 = 0;
   if (n == 1) return true;
   int m = n;
   std::vector<int> r;
@@ -120,6 +121,13 @@ bool factor_fft(int n, FftPlan* pl) {
   if (m != 1 || (int)r.size() > kMaxStages) return false;
   pl->nst = (int)r.size();
   for (int i = 0; i < pl->nst; ++i) pl->rad[i] = r[i];
+  pl->n1 = pl->n2 = 0;
+  for (int n1 : {16, 8})
+    if (n % n1 == 0 && fft2p_supported(n1, n / n1)) {
+      pl->n1 = n1;
+      pl->n2 = n / n1;
+      break;
+    }
   return true;
 }
 

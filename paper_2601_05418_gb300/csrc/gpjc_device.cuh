@@ -183,13 +183,13 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ src, f
   }
 }
 
-// Batched ping-pong FFT (unnormalised) of `batch` transforms whose starts
-// are `bs` elements apart.  Data starts in `a`; returns the buffer holding
-// the result (a or b).  SIGN = -1 forward, +1 inverse.  Must be called by
-// all threads of the block; ends with __syncthreads().
+// Batched ping-pong Stockham FFT (unnormalised) of `batch` transforms whose
+// starts are `bs` elements apart.  Data starts in `a`; returns the buffer
+// holding the result (a or b).  SIGN = -1 forward, +1 inverse.  Must be
+// called by all threads of the block; ends with __syncthreads().
 template <int SIGN, bool PAD = false>
-__device__ float2* fft_batch(float2* a, float2* b, int batch, int bs, const FftPlan& pl,
-                             const float2* __restrict__ tw, int tid, int nthr) {
+__device__ float2* fft_stockham(float2* a, float2* b, int batch, int bs, const FftPlan& pl,
+                                const float2* __restrict__ tw, int tid, int nthr) {
   int ns = 1;
   for (int st = 0; st < pl.nst; ++st) {
     const int R = pl.rad[st];
@@ -208,6 +208,23 @@ __device__ float2* fft_batch(float2* a, float2* b, int batch, int bs, const FftP
     ns *= R;
   }
   return a;
+}
+
+}  // namespace gpjc
+#include "gpjc_fft.cuh"
+namespace gpjc {
+
+// Batched FFT of `batch` transforms of length pl.n (starts `bs` apart, data in
+// `a`, scratch `b`; returns the buffer with the result).  Lengths with a
+// two-pass plan (pl.n1 > 0; the table `tw` then holds exp(-2 pi i i2 k1 / n)
+// at k1 n2 + i2) run the register two-pass kernel, the others the radix
+// stages (`tw` holds exp(-2 pi i k / n)).  Must be called by all threads of
+// the block; ends with __syncthreads().
+template <int SIGN, bool PAD = false>
+__device__ __forceinline__ float2* fft_batch(float2* a, float2* b, int batch, int bs, const FftPlan& pl,
+                                             const float2* __restrict__ tw, int tid, int nthr) {
+  if (pl.n1 > 0 && fft2p_dispatch<SIGN, PAD>(pl.n1, pl.n2, a, b, batch, bs, tw, tid, nthr)) return a;
+  return fft_stockham<SIGN, PAD>(a, b, batch, bs, pl, tw, tid, nthr);
 }
 
 // ------------------------------------------------------------ reductions --

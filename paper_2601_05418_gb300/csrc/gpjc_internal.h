@@ -13,7 +13,17 @@ struct FftPlan {
   int n;
   int nst;
   int rad[kMaxStages];
+  int n1, n2;  // two-pass plan n = n1 n2 (0 when n has none; then the radix stages run)
 };
+
+// Lengths that have a two-pass FFT plan n = n1 n2 (the list is shared by the
+// host planner and the device dispatcher).
+__host__ __device__ constexpr int fft2p_code(int n1, int n2) { return n1 * 64 + n2; }
+__host__ __device__ constexpr bool fft2p_supported(int n1, int n2) {
+  return (n1 == 16 && (n2 == 8 || n2 == 10 || n2 == 12 || n2 == 14 || n2 == 15 || n2 == 16 || n2 == 18 ||
+                       n2 == 20)) ||
+         (n1 == 8 && (n2 == 5 || n2 == 7));
+}
 
 // Geometry and device-resident bookkeeping tables, passed to kernels by
 // value.  All pointers are device pointers owned by the plan.

@@ -19,29 +19,36 @@
 namespace gpjc {
 
 // ------------------------------------------------------------------ tables --
-__global__ void k_make_tables(int nx, int ny, int nz, int os, float2* tw_x, float2* tw_y, float2* tw_z,
-                              float2* pre, float* ay, float* az, double cycles, double kappa_y,
-                              double kappa_z) {
+// Twiddle table of one FFT length n: exp(-2 pi i e / n) at position k, with
+// e = k for the radix-stage plan and e = (k mod n2) (k / n2) for the two-pass
+// plan n = n1 n2 (position k1 n2 + i2 holds the twiddle of i2 k1).
+__device__ __forceinline__ float2 fft_twiddle(int k, int n, int n2) {
+  const int e = n2 > 0 ? (k % n2) * (k / n2) : k;
+  double s, c;
+  sincospi(-2.0 * (double)e / n, &s, &c);
+  return make_float2((float)c, (float)s);
+}
+
+__global__ void k_make_tables(int nx, int ny, int nz, int os, int n2x, int n2y, int n2z, float2* tw_x,
+                              float2* tw_y, float2* tw_z, float2* pre, float* ay, float* az, double cycles,
+                              double kappa_y, double kappa_z) {
   const int ntx = os * nx;
   const int total = nx + ny + nz + ntx + ntx;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     double s, c;
     int k = i;
     if (k < nx) {
-      sincospi(-2.0 * k / nx, &s, &c);
-      tw_x[k] = make_float2((float)c, (float)s);
+      tw_x[k] = fft_twiddle(k, nx, n2x);
       continue;
     }
     k -= nx;
     if (k < ny) {
-      sincospi(-2.0 * k / ny, &s, &c);
-      tw_y[k] = make_float2((float)c, (float)s);
+      tw_y[k] = fft_twiddle(k, ny, n2y);
       continue;
     }
     k -= ny;
     if (k < nz) {
-      sincospi(-2.0 * k / nz, &s, &c);
-      tw_z[k] = make_float2((float)c, (float)s);
+      tw_z[k] = fft_twiddle(k, nz, n2z);
       continue;
     }
     k -= nz;
@@ -66,8 +73,9 @@ __global__ void k_make_tables(int nx, int ny, int nz, int os, float2* tw_x, floa
 cudaError_t launch_make_tables(Geo& g, float2* tw_x, float2* tw_y, float2* tw_z, float2* pre, float* ay,
                                float* az, double cycles, double kappa_y, double kappa_z, cudaStream_t st) {
   const int total = g.nx + g.ny + g.nz + 2 * g.ntx;
-  note_launches(1); k_make_tables<<<(total + 255) / 256, 256, 0, st>>>(g.nx, g.ny, g.nz, g.os, tw_x, tw_y, tw_z, pre, ay, az,
-                                                     cycles, kappa_y, kappa_z);
+  note_launches(1); k_make_tables<<<(total + 255) / 256, 256, 0, st>>>(g.nx, g.ny, g.nz, g.os, g.fx.n2, g.fy.n2,
+                                                                      g.fz.n2, tw_x, tw_y, tw_z, pre, ay, az,
+                                                                      cycles, kappa_y, kappa_z);
   return cudaGetLastError();
 }
 
