@@ -321,23 +321,38 @@ extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
     rh.G = G; rh.w = w; rh.ntx = (int)ntx; rh.ntxc = p->ntxc;
     rh.pg = p->pg; rh.keep = p->keep; rh.poff = p->poff; rh.aoff = p->aoff;
     for (int adj = 0; adj < 2; ++adj) {
-      int best = 0;
-      for (int rb = 1; rb <= 8; rb *= 2) {
-        const int nt = readout_tile_count(rh, rb, adj != 0);
-        const size_t smem = adj ? readout_adj_smem(g, rb) : readout_fwd_smem(g, rb);
-        if (smem > 110 * 1024 || (nt + 255) / 256 > (adj ? 4 : 3) || rb > g.rows) break;
-        if (adj && (rb * nx + 255) / 256 > 8) break;
-        best = rb;
-        if (nt >= 256) break;
+      int best = 0, ts = 4, hstage = 0;
+      // adjoint: one row per block with its row of H2 in shared memory, when
+      // that leaves room for three blocks per SM (tiles of 2 samples if 4
+      // leave threads without a tile)
+      if (adj && readout_adj_smem(g, 1, 1) <= 74 * 1024 && nx <= 512) {
+        best = 1;
+        hstage = 1;
+        ts = readout_tile_count(rh, 1, true, 4) >= 256 ? 4 : 2;
+        if ((readout_tile_count(rh, 1, true, ts) + 255) / 256 > 4) best = 0;
+      }
+      if (!best) {
+        ts = 4;
+        hstage = 0;
+        for (int rb = 1; rb <= 8; rb *= 2) {
+          const int nt = readout_tile_count(rh, rb, adj != 0, 4);
+          const size_t smem = adj ? readout_adj_smem(g, rb, 0) : readout_fwd_smem(g, rb);
+          if (smem > 110 * 1024 || (nt + 255) / 256 > (adj ? 4 : 3) || rb > g.rows) break;
+          if (adj && (rb * nx + 255) / 256 > 8) break;
+          best = rb;
+          if (nt >= 256) break;
+        }
       }
       RTiles& rt = adj ? p->rt_a : p->rt_f;
       rt.rb = best;
       rt.nt = 0;
+      rt.ts = ts;
+      rt.hstage = hstage;
       rt.hdr = nullptr;
       rt.cols = nullptr;
       if (best) {
         std::vector<int4> hdr, cols;
-        build_readout_tiles(rh, best, adj != 0, &hdr, &cols);
+        build_readout_tiles(rh, best, adj != 0, ts, &hdr, &cols);
         int4 *dh, *dc;
         if ((s = m.upload(&dh, hdr)) || (s = m.upload(&dc, cols))) return s;
         rt.nt = (int)hdr.size();
@@ -1334,6 +1349,7 @@ extern "C" gpjc_status gpjc_batch_create(int32_t n, gpjc_op* const* ops, int32_t
     s.mt_f = (p->rt_f.nt + 255) / 256;
     const int mx = (p->rt_a.rb * g.nx + 255) / 256;
     s.mx_a = mx <= 1 ? 1 : mx <= 2 ? 2 : mx <= 4 ? 4 : 8;
+    if (p->rt_a.ts == 2) s.mx_a = mx <= 1 ? 5 : 6;  // two-sample tiles (one row per block)
     if (mx > 8) return fail(GPJC_EUNSUPPORTED, "slice %d: adjoint rows too wide", i);
     s.coil = op->coil;
     s.AT = op->gr->AT;
@@ -1343,7 +1359,7 @@ extern "C" gpjc_status gpjc_batch_create(int32_t n, gpjc_op* const* ops, int32_t
     s.xparts = op->xparts;
     s.r = op->vr;
     s.p = op->vp;
-    smem = std::max(smem, std::max(readout_fwd_smem(g, p->rt_f.rb), readout_adj_smem(g, p->rt_a.rb)));
+    smem = std::max(smem, std::max(readout_fwd_smem(g, p->rt_f.rb), readout_adj_smem(g, p->rt_a.rb, p->rt_a.hstage)));
     smem = std::max(smem, batch_pe_smem(g));
   }
   b->smem = smem;

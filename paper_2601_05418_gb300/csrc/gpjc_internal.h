@@ -60,6 +60,8 @@ struct Geo {
 struct RTiles {
   int rb;
   int nt;
+  int ts;            // adjoint: readout samples per tile (2 or 4)
+  int hstage;        // adjoint: the block's rows of H2 are staged in shared memory (rb == 1)
   const int4* hdr;   // [nt]
   const int4* cols;  // [nt * 4]
 };

@@ -40,11 +40,11 @@ struct ReadoutGeomHost {
   int G, w, ntx, ntxc;
   std::vector<int> pg, keep, poff, aoff;
 };
-void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, std::vector<int4>* hdr,
+void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, int ts, std::vector<int4>* hdr,
                          std::vector<int4>* cols);
-int readout_tile_count(const ReadoutGeomHost& h, int rb, bool adjoint);
+int readout_tile_count(const ReadoutGeomHost& h, int rb, bool adjoint, int ts);
 size_t readout_fwd_smem(const Geo& g, int rb);
-size_t readout_adj_smem(const Geo& g, int rb);
+size_t readout_adj_smem(const Geo& g, int rb, int hstage);
 cudaError_t launch_k1f_tiled(const Geo& g, const RTiles& tl, const float2* x, const float2* coil,
                              const float2* AT, float2* Hpart, int nchunk, cudaStream_t st);
 cudaError_t launch_k1a_tiled(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,

@@ -29,9 +29,15 @@ size_t readout_fwd_smem(const Geo& g, int rb) {
   const int st = u_stride(g.ntx);
   return sizeof(float2) * (size_t)(spad_size(rb * st) + 2 * spad_size(g.ntx) + g.nx);
 }
-size_t readout_adj_smem(const Geo& g, int rb) {
+// staged H2 rows: one padding slot every 16 columns (conflict-free when the
+// tiles of a warp read columns 16 kept components apart)
+__host__ __device__ inline int hpad(int i) { return i + (i >> 4); }
+__host__ __device__ inline int hpad_size(int n) { return n + (n >> 4) + 1; }
+
+size_t readout_adj_smem(const Geo& g, int rb, int hstage) {
   const int st = u_stride(g.ntx);
-  return sizeof(float2) * (size_t)(spad_size(rb * st) + spad_size(g.ntx) + g.nx);
+  return sizeof(float2) *
+         (size_t)(spad_size(rb * st) + spad_size(g.ntx) + g.nx + (hstage ? hpad_size(rb * g.ntxc) : 0));
 }
 
 __device__ __forceinline__ float2 post_at(const Geo& g, int t, int row) {
@@ -157,7 +163,7 @@ __global__ void __launch_bounds__(kRThreads) k1f_tiled(Geo g, RTiles tl, const f
 }
 
 // ------------------------------------------------------------------ adjoint --
-template <int MAXX, bool P>
+template <int MAXX, bool P, int TS>
 __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const float2* __restrict__ H2,
                                          const float2* __restrict__ coil, const float2* __restrict__ Arow,
                                          float2* __restrict__ xpart, int cpc, int rblock, int chunk,
@@ -166,11 +172,18 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
   float2* U = rsm;
   float2* B = U + spad_size(rb * st);
   float2* tw = B + spad_size(g.ntx);
+  float2* Hs = tw + g.nx;  // staged H2 rows (tl.hstage)
   const int row0 = rblock * rb;
   const int nrows = min(rb, g.rows - row0);
   for (int i = threadIdx.x; i < g.nx; i += blockDim.x) tw[i] = g.tw_x[i];
   const size_t L = (size_t)g.rows * g.nx;
   const int nx = g.nx, os = g.os, w = g.w, ns = g.ns;
+  const bool hs = tl.hstage != 0;
+  if (hs) {
+    // the block's rows of H2, read once for all coils of the chunk
+    const float2* src = H2 + (size_t)row0 * g.ntxc;
+    for (int i = threadIdx.x; i < nrows * g.ntxc; i += blockDim.x) Hs[hpad(i)] = ldm<P>(src + i);
+  }
 
   float2 xacc[MAXX];
 #pragma unroll
@@ -178,34 +191,41 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
   __syncthreads();
   const int n0 = chunk * cpc, n1 = min(g.nc, n0 + cpc);
   for (int n = n0; n < n1; ++n) {
-    // A^H on every tile: U_r[t] = sum_k conj(A_g[k][n w + tau]) H2[row][off_p + k];
-    // the tile descriptors are re-read (L1) to keep registers for the sums
+    // A^H on every tile: U_r[t] = sum_k conj(A_g[k][n w + tau]) H2[row][off_p + k]
+    // (TS samples x 4 columns per tile); the tile descriptors are re-read
+    // (L1) to keep registers for the sums
     for (int tile = threadIdx.x; tile < tl.nt; tile += kRThreads) {
       const int4 h = tl.hdr[tile];  // (aoff_g + tau0, keep_g, tcnt, unused)
-      int cr[4];
+      int cr[4], hoff[4];
       const float2* hp[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int4 cc = tl.cols[tile * 4 + c];  // (r, off_p, p w + tau0, 0)
         cr[c] = (cc.x >= 0 && cc.x < nrows) ? cc.x : -1;
         hp[c] = cr[c] >= 0 ? H2 + (size_t)(row0 + cc.x) * g.ntxc + cc.y : H2;
+        hoff[c] = cr[c] >= 0 ? cc.x * g.ntxc + cc.y : 0;
       }
-      float2 acc[4][4];
+      float2 acc[4][TS];
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) acc[c][k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < TS; ++k) acc[c][k] = make_float2(0.f, 0.f);
       const float2* Ap = Arow + h.x + n * w;
       for (int k = 0; k < h.y; ++k) {
-        float2 a[4], hv[4];
+        float2 a[TS], hv[4];
 #pragma unroll
-        for (int tt = 0; tt < 4; ++tt) a[tt] = tt < h.z ? __ldg(Ap + tt) : make_float2(0.f, 0.f);
+        for (int tt = 0; tt < TS; ++tt) a[tt] = tt < h.z ? __ldg(Ap + tt) : make_float2(0.f, 0.f);
+        if (hs) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) hv[c] = cr[c] >= 0 ? ldm<P>(hp[c] + k) : make_float2(0.f, 0.f);
+          for (int c = 0; c < 4; ++c) hv[c] = cr[c] >= 0 ? Hs[hpad(hoff[c] + k)] : make_float2(0.f, 0.f);
+        } else {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) hv[c] = cr[c] >= 0 ? ldm<P>(hp[c] + k) : make_float2(0.f, 0.f);
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
-          for (int tt = 0; tt < 4; ++tt) cfmac(acc[c][tt], a[tt], hv[c]);
+          for (int tt = 0; tt < TS; ++tt) cfmac(acc[c][tt], a[tt], hv[c]);
         Ap += ns;
       }
 #pragma unroll
@@ -217,7 +237,7 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
         const float2* py = g.post_y + (size_t)(row % g.ny) * g.ntx;
         const float2* pz = g.post_z + (size_t)(row / g.ny) * g.ntx;
 #pragma unroll
-        for (int tt = 0; tt < 4; ++tt) {
+        for (int tt = 0; tt < TS; ++tt) {
           if (tt >= h.z) continue;
           const int t = t0 + tt;
           const int mm = t / os, s = t - mm * os;
@@ -254,13 +274,13 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
   }
 }
 
-template <int MAXX>
+template <int MAXX, int TS>
 __global__ void __launch_bounds__(kRThreads) k1a_tiled(Geo g, RTiles tl, const float2* __restrict__ H2,
                                                        const float2* __restrict__ coil,
                                                        const float2* __restrict__ Arow, float2* __restrict__ xpart,
                                                        int cpc) {
   extern __shared__ float2 rsm[];
-  k1a_body<MAXX, false>(g, tl, H2, coil, Arow, xpart, cpc, blockIdx.x, blockIdx.y, rsm);
+  k1a_body<MAXX, false, TS>(g, tl, H2, coil, Arow, xpart, cpc, blockIdx.x, blockIdx.y, rsm);
 }
 
 }  // namespace gpjc
@@ -270,7 +290,7 @@ namespace gpjc {
 // ------------------------------------------------------------------ host side --
 static int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
-void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, std::vector<int4>* hdr,
+void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, int ts, std::vector<int4>* hdr,
                          std::vector<int4>* cols) {
   const int st = u_stride(h.ntx);
   std::vector<std::vector<int>> occ(h.G);
@@ -281,9 +301,10 @@ void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, std::ve
     const int oc = (int)occ[g].size();
     const int ncol = rb * oc;
     const int inner = adjoint ? h.w : h.keep[g];  // samples (adjoint) or kept components (forward)
-    for (int i0 = 0; i0 < inner; i0 += 4) {
+    const int step = adjoint ? ts : 4;
+    for (int i0 = 0; i0 < inner; i0 += step) {
       for (int c0 = 0; c0 < ncol; c0 += 4) {
-        hdr->push_back(make_int4(h.aoff[g] + i0, h.keep[g], std::min(4, inner - i0), 0));
+        hdr->push_back(make_int4(h.aoff[g] + i0, h.keep[g], std::min(step, inner - i0), 0));
         for (int c = 0; c < 4; ++c) {
           const int cc = c0 + c;
           if (cc >= ncol) {
@@ -301,12 +322,12 @@ void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, std::ve
   }
 }
 
-int readout_tile_count(const ReadoutGeomHost& h, int rb, bool adjoint) {
+int readout_tile_count(const ReadoutGeomHost& h, int rb, bool adjoint, int ts) {
   std::vector<std::vector<int>> occ(h.G);
   for (int p = 0; p < (int)h.pg.size(); ++p) occ[h.pg[p]].push_back(p);
   int n = 0;
   for (int g = 0; g < h.G; ++g)
-    n += ceil_div(adjoint ? h.w : h.keep[g], 4) * ceil_div(rb * (int)occ[g].size(), 4);
+    n += ceil_div(adjoint ? h.w : h.keep[g], adjoint ? ts : 4) * ceil_div(rb * (int)occ[g].size(), 4);
   return n;
 }
 
@@ -335,29 +356,34 @@ cudaError_t launch_k1f_tiled(const Geo& g, const RTiles& tl, const float2* x, co
   return cudaErrorInvalidValue;
 }
 
-template <int MAXX>
+template <int MAXX, int TS>
 static cudaError_t launch_a(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,
                             const float2* A, float2* xpart, int nchunk, cudaStream_t st) {
   const int cpc = (g.nc + nchunk - 1) / nchunk;
-  const size_t sm = readout_adj_smem(g, tl.rb);
+  const size_t sm = readout_adj_smem(g, tl.rb, tl.hstage);
   static int attr = 0;
   if ((int)sm > attr) {
-    cudaFuncSetAttribute(k1a_tiled<MAXX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k1a_tiled<MAXX>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k1a_tiled<MAXX, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k1a_tiled<MAXX, TS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr = (int)sm;
   }
   dim3 grid((g.rows + tl.rb - 1) / tl.rb, nchunk);
-  note_launches(1); k1a_tiled<MAXX><<<grid, kRThreads, sm, st>>>(g, tl, H2, coil, A, xpart, cpc);
+  note_launches(1); k1a_tiled<MAXX, TS><<<grid, kRThreads, sm, st>>>(g, tl, H2, coil, A, xpart, cpc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_k1a_tiled(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,
                              const float2* A, float2* xpart, int nchunk, cudaStream_t st) {
   const int mx = ceil_div(tl.rb * g.nx, kRThreads);
-  if (mx <= 1) return launch_a<1>(g, tl, H2, coil, A, xpart, nchunk, st);
-  if (mx <= 2) return launch_a<2>(g, tl, H2, coil, A, xpart, nchunk, st);
-  if (mx <= 4) return launch_a<4>(g, tl, H2, coil, A, xpart, nchunk, st);
-  if (mx <= 8) return launch_a<8>(g, tl, H2, coil, A, xpart, nchunk, st);
+  if (tl.ts == 2) {
+    if (mx <= 1) return launch_a<1, 2>(g, tl, H2, coil, A, xpart, nchunk, st);
+    if (mx <= 2) return launch_a<2, 2>(g, tl, H2, coil, A, xpart, nchunk, st);
+    return cudaErrorInvalidValue;
+  }
+  if (mx <= 1) return launch_a<1, 4>(g, tl, H2, coil, A, xpart, nchunk, st);
+  if (mx <= 2) return launch_a<2, 4>(g, tl, H2, coil, A, xpart, nchunk, st);
+  if (mx <= 4) return launch_a<4, 4>(g, tl, H2, coil, A, xpart, nchunk, st);
+  if (mx <= 8) return launch_a<8, 4>(g, tl, H2, coil, A, xpart, nchunk, st);
   return cudaErrorInvalidValue;
 }
 
@@ -407,10 +433,12 @@ __device__ __forceinline__ void batch_readout(const BatchSlice& s, const Geo& g,
       k1f_body<2, true>(g, s.rtf, s.p, s.coil, s.AT, s.Hpart, s.cpc, rblock, chunk, sm);
   } else {
     switch (s.mx_a) {
-      case 1: k1a_body<1, true>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
-      case 2: k1a_body<2, true>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
-      case 4: k1a_body<4, true>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
-      default: k1a_body<8, true>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
+      case 1: k1a_body<1, true, 4>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
+      case 2: k1a_body<2, true, 4>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
+      case 4: k1a_body<4, true, 4>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
+      case 5: k1a_body<1, true, 2>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
+      case 6: k1a_body<2, true, 2>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
+      default: k1a_body<8, true, 4>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
     }
   }
 }
