@@ -395,7 +395,7 @@ struct gpjc_groups {
   bool keep_gram;
   int b, iters, iters32, nblk, Kpad;
   float2 *P32, *X32, *Y32;  // FP32 phase of the subspace iteration
-  int2* tg_pairs;           // (128-row, 64-column) tile pairs of the tensor-core Gram
+  int2* tg_pairs;           // coil pairs (n, n'), n <= n', of the tensor-core Gram
   int tg_npairs;
   bool tc_gram;             // tensor-core Gram (default) or the FFMA one
   // scratch kept for rebuilds, so a rebuild allocates nothing and does
@@ -460,8 +460,8 @@ static gpjc_status groups_compute(gpjc_groups* gr, const float2* coil, const uin
   CK(launch_roi_coils(g, coil, h_T ? gr->dT : nullptr, gr->pix, gr->dK, gr->Kpad, gr->chat, st));
   CK(cudaMemsetAsync(gr->P, 0, sizeof(double2) * (size_t)g.G * g.ns * g.ns, st));
   if (gr->tc_gram)
-    CK(launch_tc_gram(g, gr->chat, gr->pix, gr->dK, gr->Kpad, gr->d_ref, gr->tg_pairs, gr->tg_npairs, gr->P,
-                      gr->tc_status, st));
+    CK(launch_tc_gram2(g, gr->chat, gr->pix, gr->dK, gr->Kpad, gr->d_ref, gr->tg_pairs, gr->tg_npairs, gr->P,
+                       gr->tc_status, st));
   else
     CK(launch_gram(g, gr->chat, gr->pix, gr->dK, gr->Kpad, gr->d_ref, gr->P, st));
   CK(launch_hermitize(g, gr->P, st));
@@ -567,11 +567,10 @@ extern "C" gpjc_status gpjc_build_groups(const gpjc_plan* plan, const float* d_c
   CK(cudaMemcpy(gr->d_ref, plan->ref.data(), sizeof(int) * g.G, cudaMemcpyHostToDevice));
   {
     const char* e = getenv("GPJC_SIMT_GRAM");
-    gr->tc_gram = !(e && e[0] == '1') && tc_gram_smem(g) <= 220 * 1024;
+    gr->tc_gram = !(e && e[0] == '1') && tc_gram2_smem(g) <= 227 * 1024;
     std::vector<int2> pairs;
-    for (int I = 0; I * 128 < g.ns; ++I)
-      for (int J = 0; J * 64 < g.ns; ++J)
-        if (J * 64 + 63 >= I * 128) pairs.push_back(make_int2(I, J));
+    for (int n = 0; n < g.nc; ++n)
+      for (int n2 = n; n2 < g.nc; ++n2) pairs.push_back(make_int2(n, n2));
     gr->tg_npairs = (int)pairs.size();
     if ((s = m.upload(&gr->tg_pairs, pairs))) return s;
     if (!gr->tc_status) {

@@ -65,10 +65,10 @@ cudaError_t launch_tc_compress(const CUtensorMap& map, const TcGeom& t, int fmt,
                                float2* out, int lines, int* status, cudaStream_t st);
 cudaError_t launch_tc_expand(const TcGeom& t, int fmt, const float2* H, const uint16_t* Bx, float2* V, int rows,
                              int* status, cudaStream_t st);
-size_t tc_gram_smem(const Geo& g);
-cudaError_t launch_tc_gram(const Geo& g, const float2* chat, const int* pix, const int* dK, int Kpad,
-                           const int* pref, const int2* pairs, int npairs, double2* P, int* status,
-                           cudaStream_t st);
+size_t tc_gram2_smem(const Geo& g);
+cudaError_t launch_tc_gram2(const Geo& g, const float2* chat, const int* pix, const int* dK, int Kpad,
+                            const int* pref, const int2* cpairs, int npairs, double2* P, int* status,
+                            cudaStream_t st);
 cudaError_t launch_sim_fwd_f16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
                                cudaStream_t st);
 cudaError_t launch_sim_adj_f16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,

@@ -141,6 +141,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+               "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+               "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+               "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // 16-bit element conversions
 template <int FMT>
 __device__ __forceinline__ uint32_t pack2(float a, float b);
@@ -536,20 +545,11 @@ cudaError_t launch_tc_expand(const TcGeom& t, int fmt, const float2* H, const ui
 }  // namespace gpjc
 
 // ====================================================================== Gram --
-// P_g = sum_r v_r v_r^H on the tensor cores (Eq. 9-11).  v is generated per
-// pixel chunk from the normalised coil values and the patch phases, scaled
-// by 2^12 and split into an FP16 head and remainder; three MMAs per K step
-// (head x head, head x rest, rest x head) keep the products at about FP32
-// accuracy.  Real embedding: A rows are i (128 per tile), K = (pixel, re/im),
-// B rows are (j, part) with part 0 = [Re v_j, Im v_j], part 1 = [-Im v_j, Re v_j],
-// so D[i][2 j' + 0] = Re P_ij and D[i][2 j' + 1] = Im P_ij.  The TMEM
-// accumulator (FP32) is drained into FP64 shared-memory sums every
-// kTgRun chunks; slabs of pixels are combined with FP64 atomics.
+// P_g = sum_r v_r v_r^H on the tensor cores (Eq. 9-11).  Values are scaled by
+// 2^12 and split into an FP16 head and remainder; three MMAs per K step (head
+// x head, head x rest, rest x head) keep the products at about FP32 accuracy.
 namespace gpjc {
 
-constexpr int kTgKC = 32;      // pixels per chunk (K = 64)
-constexpr int kTgRun = 8;      // chunks per FP32 run (256 pixels)
-constexpr int kTgSlab = 4096;  // pixels per block
 constexpr float kTgScale = 4096.0f;  // 2^12 before the split; products carry 2^24
 
 __device__ __forceinline__ void split_f16(float a, float b, uint32_t* hi, uint32_t* lo) {
@@ -560,153 +560,311 @@ __device__ __forceinline__ void split_f16(float a, float b, uint32_t* hi, uint32
   *lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_tc_gram(Geo g, const float2* __restrict__ chat,
-                                                          const int* __restrict__ pix,
-                                                          const int* __restrict__ dK, int Kpad,
-                                                          const int* __restrict__ pref,
-                                                          const int2* __restrict__ pairs,
-                                                          double2* __restrict__ P, int* status) {
+// ---------------------------------------------------------------- Gram (C x Psi) --
+// The patch vector of pixel r is v_r = c_hat(r) (x) psi_g(r) (coil-major), so
+//   P_g[(n, tau), (n', tau')] = sum_r C_{n n'}(r) Psi_{g tau tau'}(r),
+//   C_{n n'} = c_hat_n conj(c_hat_n'),  Psi_{g tau tau'} = psi_{g tau} conj(psi_{g tau'}).
+// One GEMM over the ROI pixels gives every group at once: M = coil pairs
+// n <= n' (shared by all groups), N = (g, tau, tau') (shared by all coil
+// pairs), so each operand value is generated once per pixel per tile instead
+// of once per (row, column) tile of every P_g.  Real embedding as above
+// (K = (pixel, re/im); B rows 2e = [Re Psi, -Im Psi], 2e+1 = [Im Psi, Re Psi]),
+// FP16 head/remainder split (three MMAs per K step), 128 x 256 tiles with a
+// 256-column TMEM accumulator, operand images double-buffered so that the
+// eight warps build chunk c+1 while the MMAs of chunk c run.  FP32 runs of at
+// most 256 pixels in the tensor memory are summed in registers, and a block
+// adds its sums to P_g with FP64 atomics when its tile changes (persistent
+// blocks over a tile-major split of the (tile, chunk) units).  Entries with
+// n > n' are filled by the Hermitian completion.
+constexpr int kTg2Threads = 512;          // 16 warps: 4 per TMEM lane quarter
+constexpr int kTg2Cols = 256 * 128 / kTg2Threads;  // accumulator columns per thread (64)
+constexpr int kTg2KC = 32;          // pixels per chunk (K = 64)
+constexpr int kTg2Px = kTg2KC * 128 / kTg2Threads;  // pixels per thread per chunk (8)
+constexpr int kTg2Run = 8;          // chunks per FP32 run in the tensor memory (256 pixels)
+constexpr int kTg2PS = kTg2KC + 1;  // row stride of the phase table (odd: no bank conflicts)
+constexpr int kTg2ImgA = 128 * 64;  // uint16 per A image
+constexpr int kTg2ImgB = 256 * 64;  // uint16 per B image
+
+__host__ __device__ inline int tg2_groups_per_tile(int w) {
+  const int w2 = w * w;
+  return (128 + w2 - 1) / w2 + 1;
+}
+
+// Tile-dependent operand rows of one thread.
+struct Tg2Rows {
+  int m, na, nb, e, gl, tau, taup, g_lo, ng;
+  bool mval, eval;
+};
+__device__ __forceinline__ Tg2Rows tg2_rows(const Geo& g, const int2* __restrict__ cpairs, int npairs, int mt,
+                                            int ntile, int row, int gpt) {
+  Tg2Rows r;
+  const int w = g.w, w2 = w * w, ne = g.G * w2;
+  r.m = mt * 128 + row;
+  r.mval = r.m < npairs;
+  r.na = r.nb = 0;
+  if (r.mval) {
+    const int2 pr = cpairs[r.m];
+    r.na = pr.x;
+    r.nb = pr.y;
+  }
+  r.e = ntile * 128 + row;
+  r.eval = r.e < ne;
+  r.g_lo = (ntile * 128) / w2;
+  const int ge = r.eval ? r.e / w2 : r.g_lo;
+  const int rem = r.eval ? r.e - ge * w2 : 0;
+  r.tau = rem / w;
+  r.taup = rem - r.tau * w;
+  r.gl = ge - r.g_lo;
+  r.ng = min(gpt, g.G - r.g_lo);
+  return r;
+}
+
+// Adds a tile's sums (this thread's TMEM lane row, kTg2Cols columns of the
+// cross-run accumulator at tacc) to P_g.
+__device__ __forceinline__ void tg2_flush(const Geo& g, const int2* __restrict__ cpairs, int npairs, int mt,
+                                          int ntile, uint32_t tacc, double2* __restrict__ P) {
+  const int warp = threadIdx.x >> 5;
+  const int w = g.w, w2 = w * w, ne = g.G * w2;
+  const double sc = 1.0 / ((double)kTgScale * (double)kTgScale);
+  const int mrow = mt * 128 + (warp & 3) * 32 + (threadIdx.x & 31);
+  const int colh = (warp >> 2) * kTg2Cols;
+  const bool ok = mrow < npairs;
+  const int2 pr = ok ? cpairs[mrow] : make_int2(0, 0);
+  for (int col = 0; col < kTg2Cols; col += 8) {
+    float v[8];
+    tmem_ld8(tacc + (uint32_t)col, v);  // all lanes take part in the collective load
+    if (!ok) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int ee = ntile * 128 + (colh + col) / 2 + j;
+      if (ee < ne) {
+        const int gg = ee / w2, rr2 = ee - gg * w2;
+        const int t1 = rr2 / w, t2 = rr2 - t1 * w;
+        double2* d = P + ((size_t)gg * g.ns + (size_t)(pr.x * w + t1)) * g.ns + (pr.y * w + t2);
+        atomicAdd(&d->x, (double)v[2 * j] * sc);
+        atomicAdd(&d->y, (double)v[2 * j + 1] * sc);
+      }
+    }
+  }
+}
+
+// Adds the finished FP32 run (TMEM columns at trun) to the cross-run
+// accumulator (columns at tacc), or copies it there for a tile's first run.
+__device__ __forceinline__ void tg2_fold(uint32_t trun, uint32_t tacc, bool first) {
+  for (int col = 0; col < kTg2Cols; col += 8) {
+    float v[8], a[8];
+    tmem_ld8(trun + (uint32_t)col, v);
+    if (!first) {
+      tmem_ld8(tacc + (uint32_t)col, a);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] += a[q];
+    }
+    tmem_st8(tacc + (uint32_t)col, v);
+  }
+  tmem_wait_st();
+}
+
+// Persistent: the (tile, 32-pixel chunk) units, tile-major, are split into
+// gridDim.x contiguous ranges (one per block), so each block sums long runs
+// of one tile and adds to P_g only when its tile changes.
+__global__ void __launch_bounds__(kTg2Threads, 1) k_tc_gram2(Geo g, const float2* __restrict__ chat,
+                                                            const int* __restrict__ pix,
+                                                            const int* __restrict__ dK, int Kpad,
+                                                            const int* __restrict__ pref,
+                                                            const int2* __restrict__ cpairs, int npairs,
+                                                            int n_tiles, int n_ntiles, double2* __restrict__ P,
+                                                            int* status) {
   extern __shared__ __align__(1024) unsigned char tsm[];
-  double* acc64 = (double*)tsm;                         // [column][row], 128 x 128
-  uint16_t* Ah = (uint16_t*)(acc64 + 128 * 128);        // 128 x 64 images
-  uint16_t* Al = Ah + 128 * 64;
-  uint16_t* Bh = Al + 128 * 64;
-  uint16_t* Bl = Bh + 128 * 64;
-  float2* psi = (float2*)(Bl + 128 * 64);               // [w][kTgKC]
-  uint64_t* bar = (uint64_t*)(psi + g.w * kTgKC);
-  uint32_t* tmem_slot = (uint32_t*)(bar + 1);
-  const int grp = blockIdx.y;
-  const int2 pr = pairs[blockIdx.x];
-  const int i0 = pr.x * 128, j0 = pr.y * 64;
+  uint16_t* img = (uint16_t*)tsm;  // [buf][Ah, Al, Bh, Bl]
+  const int gpt = tg2_groups_per_tile(g.w);
+  float2* psi = (float2*)(img + 2 * (2 * kTg2ImgA + 2 * kTg2ImgB));  // [gl][tau][px], rows kTg2PS apart
+  int4* pxy = (int4*)(((uintptr_t)(psi + gpt * g.w * kTg2PS) + 15) & ~(uintptr_t)15);  // chunk pixels (x, y, z, valid)
+  uint64_t* bars = (uint64_t*)(pxy + kTg2KC);
+  uint32_t* tmem_slot = (uint32_t*)(bars + 2);
+  const int w = g.w;
   const int K = *dK;
-  const int kend_all = ((K + kTgKC - 1) / kTgKC) * kTgKC;
-  const int k_begin = blockIdx.z * kTgSlab;
-  const int k_end = min(kend_all, k_begin + kTgSlab);
-  if (k_begin >= k_end) return;
+  const int nck = (K + kTg2KC - 1) / kTg2KC;
+  const long long U = (long long)n_tiles * nck;
+  const long long u0 = U * blockIdx.x / gridDim.x, u1 = U * (blockIdx.x + 1) / gridDim.x;
+  if (u0 >= u1) return;
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
-    mbar_init(bar, 1);
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) tmem_alloc(tmem_slot, 128);
-  for (int i = tid; i < 128 * 128; i += kTcThreads) acc64[i] = 0.0;
+  if (warp == 0) tmem_alloc(tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = idesc_f16(0, 128);
+  const uint32_t idesc = idesc_f16(0, 256);
   const uint32_t sbo = (64 / 8) * 128;
-  const int t0 = pref[grp] * g.w;
   const float inv_ny = 1.0f / (float)g.ny, inv_nz = 1.0f / (float)g.nz;
-  // this thread's A row i and B row (j, part)
-  const int ia = i0 + tid;
-  const int na = ia / g.w, taua = ia - na * g.w;
-  const int jb = j0 + (tid >> 1), part = tid & 1;
-  const int nb = jb / g.w, taub = jb - nb * g.w;
-  uint32_t phase = 0;
+  const int row = tid & 127, quarter = tid >> 7;
+  // this thread's share of the MMA accumulator (columns 0-255: one FP32 run
+  // of at most kTg2Run chunks = 256 pixels) and of the cross-run FP32 sum
+  // (columns 256-511): TMEM lane row, kTg2Cols columns
+  const uint32_t tm_row = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * kTg2Cols);
+  const uint32_t tm_acc = tm_row + 256u;
+  bool acc_first = true;
+  uint32_t par[2] = {0u, 0u};
+  bool pend[2] = {false, false};
   bool ok = true;
-  int run = 0;
-  for (int k0 = k_begin; k0 < k_end && ok; k0 += kTgKC) {
-    for (int idx = tid; idx < g.w * kTgKC; idx += kTcThreads) {
-      const int tau = idx / kTgKC, r = idx - tau * kTgKC;
-      const int k = k0 + r;
-      float2 e = make_float2(0.f, 0.f);
+  int c = 0, run = 0;
+  int cur = -1;  // tile of the chunks in flight / in the registers
+  Tg2Rows R;
+  for (long long u = u0; u < u1; ++u, ++c) {
+    const int tile = (int)(u / nck);
+    const int k0 = (int)(u - (long long)tile * nck) * kTg2KC;
+    const int buf = c & 1;
+    uint16_t* Ah = img + buf * (2 * kTg2ImgA + 2 * kTg2ImgB);
+    uint16_t* Al = Ah + kTg2ImgA;
+    uint16_t* Bh = Al + kTg2ImgA;
+    uint16_t* Bl = Bh + kTg2ImgB;
+    if (pend[buf]) {  // the MMAs of chunk c - 2 read this buffer
+      if (!(ok = block_wait(&bars[buf], par[buf]))) break;
+      pend[buf] = false;
+    }
+    const int mt = tile / n_ntiles, ntile = tile - mt * n_ntiles;
+    if (tile != cur) R = tg2_rows(g, cpairs, npairs, mt, ntile, row, gpt);
+    // the chunk's pixel coordinates, then the phases psi_{g tau}(r) of the
+    // tile's groups
+    if (tid < kTg2KC) {
+      const int k = k0 + tid;
+      int4 q = make_int4(0, 0, 0, 0);
       if (k < K) {
         const int p = pix[k];
-        const int x = p % g.nx, row = p / g.nx;
-        const int y = row % g.ny, z = row / g.ny;
-        const int t = t0 + tau;
-        int prod = ((t - g.ntx / 2) * (x - g.nx / 2)) % g.ntx;
-        if (prod < 0) prod += g.ntx;
-        const float wave = g.ay[t] * (float)(y - g.ny / 2) * inv_ny +
-                           (g.nz > 1 ? g.az[t] * (float)(z - g.nz / 2) * inv_nz : 0.0f);
-        e = expipi(-(2.0f * (float)prod / (float)g.ntx + 2.0f * wave));
+        const int rw = p / g.nx;
+        q = make_int4(p - rw * g.nx - g.nx / 2, rw % g.ny - g.ny / 2, rw / g.ny - g.nz / 2, 1);
       }
-      psi[idx] = e;
+      pxy[tid] = q;
     }
     __syncthreads();
-    for (int r = 0; r < kTgKC; ++r) {
-      float2 va = make_float2(0.f, 0.f), vb = make_float2(0.f, 0.f);
-      if (ia < g.ns) va = cscale(cmul(chat[(size_t)na * Kpad + k0 + r], psi[taua * kTgKC + r]), kTgScale);
-      if (jb < g.ns) vb = cscale(cmul(chat[(size_t)nb * Kpad + k0 + r], psi[taub * kTgKC + r]), kTgScale);
-      uint32_t h, l;
-      split_f16(va.x, va.y, &h, &l);
-      *(uint32_t*)(Ah + core_off(tid, 2 * r, 64)) = h;
-      *(uint32_t*)(Al + core_off(tid, 2 * r, 64)) = l;
-      if (part == 0)
-        split_f16(vb.x, vb.y, &h, &l);
-      else
-        split_f16(-vb.y, vb.x, &h, &l);
-      *(uint32_t*)(Bh + core_off(tid, 2 * r, 64)) = h;
-      *(uint32_t*)(Bl + core_off(tid, 2 * r, 64)) = l;
+    for (int idx = tid; idx < R.ng * w * kTg2KC; idx += kTg2Threads) {
+      const int gt = idx / kTg2KC, r = idx - gt * kTg2KC;
+      const int gg = R.g_lo + gt / w, tt = gt - (gt / w) * w;
+      const int4 q = pxy[r];
+      float2 ph = make_float2(0.f, 0.f);
+      if (q.w) {
+        const int t = pref[gg] * w + tt;
+        int prod = ((t - g.ntx / 2) * q.x) % g.ntx;
+        if (prod < 0) prod += g.ntx;
+        const float wave = g.ay[t] * (float)q.y * inv_ny + (g.nz > 1 ? g.az[t] * (float)q.z * inv_nz : 0.0f);
+        ph = expipi(-(2.0f * (float)prod / (float)g.ntx + 2.0f * wave));
+      }
+      psi[gt * kTg2PS + r] = ph;
     }
+    __syncthreads();
+    const float2* pa = psi + (R.gl * w + R.tau) * kTg2PS;
+    const float2* pb = psi + (R.gl * w + R.taup) * kTg2PS;
+    const float2* ca = chat + (size_t)R.na * Kpad + k0;
+    const float2* cb = chat + (size_t)R.nb * Kpad + k0;
+    // four pixels (8 K values = one 16-byte core-matrix row) per store; the
+    // part-1 pair (Im Psi, Re Psi) is the part-0 pair (Re Psi, -Im Psi) with
+    // its two halves swapped and the new first (low) half negated (FP16
+    // rounding is symmetric, so head and remainder transform alike)
+#pragma unroll 1
+    for (int q4 = 0; q4 < kTg2Px / 4; ++q4) {
+      const int r0 = quarter * kTg2Px + 4 * q4;
+      uint32_t ah[4], al[4], b0h[4], b0l[4], b1h[4], b1l[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = r0 + j;
+        float2 cv = make_float2(0.f, 0.f), pv = make_float2(0.f, 0.f);
+        if (R.mval) cv = cscale(cmulc(cb[r], ca[r]), kTgScale);
+        if (R.eval) pv = cscale(cmulc(pb[r], pa[r]), kTgScale);
+        split_f16(cv.x, cv.y, &ah[j], &al[j]);
+        split_f16(pv.x, -pv.y, &b0h[j], &b0l[j]);
+        b1h[j] = __byte_perm(b0h[j], 0, 0x1032) ^ 0x00008000u;
+        b1l[j] = __byte_perm(b0l[j], 0, 0x1032) ^ 0x00008000u;
+      }
+      const int kk = 2 * r0;
+      *(uint4*)(Ah + core_off(row, kk, 64)) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
+      *(uint4*)(Al + core_off(row, kk, 64)) = make_uint4(al[0], al[1], al[2], al[3]);
+      *(uint4*)(Bh + core_off(2 * row, kk, 64)) = make_uint4(b0h[0], b0h[1], b0h[2], b0h[3]);
+      *(uint4*)(Bl + core_off(2 * row, kk, 64)) = make_uint4(b0l[0], b0l[1], b0l[2], b0l[3]);
+      *(uint4*)(Bh + core_off(2 * row + 1, kk, 64)) = make_uint4(b1h[0], b1h[1], b1h[2], b1h[3]);
+      *(uint4*)(Bl + core_off(2 * row + 1, kk, 64)) = make_uint4(b1l[0], b1l[1], b1l[2], b1l[3]);
+    }
+    // a run closes at kTg2Run chunks or at a tile change: add its FP32 sums
+    // to the registers (and, at a tile change, the registers to P_g) before
+    // the next MMA overwrites the accumulator
+    const bool run_start = (tile != cur) || run == kTg2Run;
+    if (run_start && c > 0) {
+      const int pb2 = (c - 1) & 1;
+      if (pend[pb2]) {
+        if (!(ok = block_wait(&bars[pb2], par[pb2]))) break;
+        pend[pb2] = false;
+      }
+      tc_fence_after();
+      tg2_fold(tm_row, tm_acc, acc_first);
+      acc_first = false;
+      if (tile != cur) {
+        tg2_flush(g, cpairs, npairs, cur / n_ntiles, cur - (cur / n_ntiles) * n_ntiles, tm_acc, P);
+        acc_first = true;
+      }
+    }
+    if (run_start) run = 0;
+    ++run;
+    cur = tile;
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     if (tid == 0) {
       tc_fence_after();
+#pragma unroll
       for (int ks = 0; ks < 4; ++ks) {
         const uint64_t ah = umma_desc(Ah + ks * 128, 128, sbo), al = umma_desc(Al + ks * 128, 128, sbo);
         const uint64_t bh = umma_desc(Bh + ks * 128, 128, sbo), bl = umma_desc(Bl + ks * 128, 128, sbo);
-        mma_f16(tmem, ah, bh, idesc, (run > 0 || ks > 0) ? 1u : 0u);
+        mma_f16(tmem, ah, bh, idesc, (!run_start || ks > 0) ? 1u : 0u);
         mma_f16(tmem, ah, bl, idesc, 1u);
         mma_f16(tmem, al, bh, idesc, 1u);
       }
-      mma_commit(bar);
+      mma_commit(&bars[buf]);
     }
-    if (!(ok = block_wait(bar, phase))) break;
-    if (++run == kTgRun || k0 + kTgKC >= k_end) {
-      run = 0;
-      tc_fence_after();
-      // drain: lane tid holds row i0 + tid, 128 FP32 columns
-      for (int col = 0; col < 128; col += 8) {
-        float v[8];
-        tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc64[(col + q) * 128 + tid] += (double)v[q];
-      }
-      tc_fence_before();
-    }
-    __syncthreads();
+    pend[buf] = true;
+  }
+  // drain: the most recent commit covers every MMA issued before it (after a
+  // timeout the accumulator is not read, only waited for before TMEM is freed)
+  if (c > 0) {
+    const int lb = (c - 1) & 1;
+    if (pend[lb] && !block_wait(&bars[lb], par[lb])) ok = false;
   }
   if (!ok) {
     if (tid == 0) atomicExch(status, (int)kDevTimeout);
-    mbar_wait(bar, phase);
-  } else {
-    const double s = 1.0 / ((double)kTgScale * (double)kTgScale);
-    double2* Pg = P + (size_t)grp * g.ns * g.ns;
-    const int i = i0 + tid;
-    if (i < g.ns)
-      for (int jj = 0; jj < 64; ++jj) {
-        const int j = j0 + jj;
-        if (j < g.ns && i <= j) {
-          double2* d = Pg + (size_t)i * g.ns + j;
-          atomicAdd(&d->x, acc64[(2 * jj) * 128 + tid] * s);
-          atomicAdd(&d->y, acc64[(2 * jj + 1) * 128 + tid] * s);
-        }
-      }
+  } else if (cur >= 0) {
+    tc_fence_after();
+    tg2_fold(tm_row, tm_acc, acc_first);
+    tg2_flush(g, cpairs, npairs, cur / n_ntiles, cur - (cur / n_ntiles) * n_ntiles, tm_acc, P);
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 128);
+  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-size_t tc_gram_smem(const Geo& g) {
-  return sizeof(double) * 128 * 128 + 4 * 128 * 64 * 2 + sizeof(float2) * (size_t)g.w * kTgKC + 64;
+size_t tc_gram2_smem(const Geo& g) {
+  return sizeof(uint16_t) * 2 * (2 * kTg2ImgA + 2 * kTg2ImgB) +
+         sizeof(float2) * (size_t)tg2_groups_per_tile(g.w) * g.w * kTg2PS + 16 + sizeof(int4) * kTg2KC + 64;
 }
 
-cudaError_t launch_tc_gram(const Geo& g, const float2* chat, const int* pix, const int* dK, int Kpad,
-                           const int* pref, const int2* pairs, int npairs, double2* P, int* status,
-                           cudaStream_t st) {
-  const size_t sm = tc_gram_smem(g);
+cudaError_t launch_tc_gram2(const Geo& g, const float2* chat, const int* pix, const int* dK, int Kpad,
+                            const int* pref, const int2* cpairs, int npairs, double2* P, int* status,
+                            cudaStream_t st) {
+  const size_t sm = tc_gram2_smem(g);
   static size_t attr = 0;
   if (sm > attr) {
-    cudaFuncSetAttribute(k_tc_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(k_tc_gram2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = sm;
   }
-  const int nslab = (Kpad + kTgSlab - 1) / kTgSlab;
-  note_launches(1); k_tc_gram<<<dim3(npairs, g.G, nslab), kTcThreads, sm, st>>>(g, chat, pix, dK, Kpad, pref, pairs,
-                                                                               P, status);
+  const int n_mtiles = (npairs + 127) / 128;
+  const int n_ntiles = (g.G * g.w * g.w + 127) / 128;
+  int dev = 0, nsm = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  note_launches(1);
+  k_tc_gram2<<<nsm, kTg2Threads, sm, st>>>(g, chat, pix, dK, Kpad, pref, cpairs, npairs, n_mtiles * n_ntiles,
+                                           n_ntiles, P, status);
   return cudaGetLastError();
 }
 
