@@ -166,6 +166,64 @@ __device__ __forceinline__ void fft2p(float2* a, float2* b, int batch, int bs, c
   __syncthreads();
 }
 
+// Two-pass transform with caller-supplied input and output: ld(f, i) returns
+// element i of transform f, st(f, k, v) receives element k (pre- and
+// post-multiplications fuse into the two passes).  `b` holds batch * n
+// scratch values; ends with __syncthreads().
+template <int N1, int N2, int SIGN, typename LD, typename ST>
+__device__ __forceinline__ void fft2p_cb(LD& ld, ST& st, float2* b, int batch, const float2* __restrict__ tw2,
+                                         int tid, int nthr) {
+  constexpr int n = N1 * N2;
+  for (int task = tid; task < batch * N2; task += nthr) {
+    const int f = task / N2, i2 = task - f * N2;
+    float2 u[N1];
+#pragma unroll
+    for (int i1 = 0; i1 < N1; ++i1) u[i1] = ld(f, N2 * i1 + i2);
+    dftr<N1, SIGN>(u);
+    float2* col = b + f * n + i2 * N1;
+    const int sw = i2 & (N1 - 1);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      float2 x = u[k1];
+      if (k1 > 0) {
+        float2 w = tw2[k1 * N2 + i2];
+        if (SIGN > 0) w.y = -w.y;
+        x = cmul(x, w);
+      }
+      col[k1 ^ sw] = x;
+    }
+  }
+  __syncthreads();
+  for (int task = tid; task < batch * N1; task += nthr) {
+    const int f = task / N1, k1 = task - f * N1;
+    float2 u[N2];
+#pragma unroll
+    for (int i2 = 0; i2 < N2; ++i2) u[i2] = b[f * n + i2 * N1 + (k1 ^ (i2 & (N1 - 1)))];
+    dftr<N2, SIGN>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) st(f, k1 + N1 * k2, u[k2]);
+  }
+  __syncthreads();
+}
+
+template <int SIGN, typename LD, typename ST>
+__device__ __forceinline__ bool fft2p_cb_dispatch(int n1, int n2, LD& ld, ST& st, float2* b, int batch,
+                                                  const float2* tw2, int tid, int nthr) {
+  switch (fft2p_code(n1, n2)) {
+    case fft2p_code(16, 8): fft2p_cb<16, 8, SIGN>(ld, st, b, batch, tw2, tid, nthr); return true;
+    case fft2p_code(16, 10): fft2p_cb<16, 10, SIGN>(ld, st, b, batch, tw2, tid, nthr); return true;
+    case fft2p_code(16, 12): fft2p_cb<16, 12, SIGN>(ld, st, b, batch, tw2, tid, nthr); return true;
+    case fft2p_code(16, 14): fft2p_cb<16, 14, SIGN>(ld, st, b, batch, tw2, tid, nthr); return true;
+    case fft2p_code(16, 15): fft2p_cb<16, 15, SIGN>(ld, st, b, batch, tw2, tid, nthr); return true;
+    case fft2p_code(16, 16): fft2p_cb<16, 16, SIGN>(ld, st, b, batch, tw2, tid, nthr); return true;
+    case fft2p_code(16, 18): fft2p_cb<16, 18, SIGN>(ld, st, b, batch, tw2, tid, nthr); return true;
+    case fft2p_code(16, 20): fft2p_cb<16, 20, SIGN>(ld, st, b, batch, tw2, tid, nthr); return true;
+    case fft2p_code(8, 5): fft2p_cb<8, 5, SIGN>(ld, st, b, batch, tw2, tid, nthr); return true;
+    case fft2p_code(8, 7): fft2p_cb<8, 7, SIGN>(ld, st, b, batch, tw2, tid, nthr); return true;
+    default: return false;
+  }
+}
+
 // Runs the two-pass plan (n1, n2); false if the pair has no instantiation.
 template <int SIGN, bool PAD>
 __device__ __forceinline__ bool fft2p_dispatch(int n1, int n2, float2* a, float2* b, int batch, int bs,

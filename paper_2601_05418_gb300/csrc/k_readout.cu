@@ -96,24 +96,39 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
       const int row = row0 + r;
       const float2* crow = coil + n * L + (size_t)row * nx;
       const float2* xrow = x + (size_t)row * nx;
-      // u = c_n x once per pixel, then its os pre-twiddled copies
-      for (int xx = threadIdx.x; xx < nx; xx += blockDim.x) {
-        const float2 u = cmul(__ldg(crow + xx), ldm<P>(xrow + xx));
-        for (int s = 0; s < os; ++s) A[spad(s * nx + xx)] = cmul(u, __ldg(g.pre + s * nx + xx));
-      }
-      __syncthreads();
-      float2* R = fft_batch<-1, true>(A, B, os, nx, g.fx, tw, threadIdx.x, blockDim.x);
       float2* Ur = U + spad(r * st);
       const float2* py = g.post_y + (size_t)(row % g.ny) * g.ntx;
       const float2* pz = g.post_z + (size_t)(row / g.ny) * g.ntx;
-      for (int m = threadIdx.x; m < nx; m += blockDim.x)
-        for (int s = 0; s < os; ++s) {
+      if (g.fx.n1 > 0) {
+        // u = c_n x once per pixel; the two-pass FFT applies the pre-twiddle
+        // while loading and the wave / centring factor while storing U
+        for (int xx = threadIdx.x; xx < nx; xx += blockDim.x) A[xx] = cmul(__ldg(crow + xx), ldm<P>(xrow + xx));
+        __syncthreads();
+        auto ld = [&](int s, int xx) { return cmul(A[xx], __ldg(g.pre + s * nx + xx)); };
+        auto stf = [&](int s, int m, float2 v) {
           const int t = m * os + s;
           float2 pt = __ldg(py + t);
           if (g.nz > 1) pt = cmul(pt, __ldg(pz + t));
-          Ur[spad(t)] = cmul(R[spad(s * nx + m)], pt);
+          Ur[spad(t)] = cmul(v, pt);
+        };
+        fft2p_cb_dispatch<-1>(g.fx.n1, g.fx.n2, ld, stf, B, os, tw, threadIdx.x, blockDim.x);
+      } else {
+        // u = c_n x once per pixel, then its os pre-twiddled copies
+        for (int xx = threadIdx.x; xx < nx; xx += blockDim.x) {
+          const float2 u = cmul(__ldg(crow + xx), ldm<P>(xrow + xx));
+          for (int s = 0; s < os; ++s) A[spad(s * nx + xx)] = cmul(u, __ldg(g.pre + s * nx + xx));
         }
-      __syncthreads();
+        __syncthreads();
+        float2* R = fft_stockham<-1, true>(A, B, os, nx, g.fx, tw, threadIdx.x, blockDim.x);
+        for (int m = threadIdx.x; m < nx; m += blockDim.x)
+          for (int s = 0; s < os; ++s) {
+            const int t = m * os + s;
+            float2 pt = __ldg(py + t);
+            if (g.nz > 1) pt = cmul(pt, __ldg(pz + t));
+            Ur[spad(t)] = cmul(R[spad(s * nx + m)], pt);
+          }
+        __syncthreads();
+      }
     }
     const int nw = n * w;
 #pragma unroll
@@ -228,11 +243,19 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
           for (int tt = 0; tt < TS; ++tt) cfmac(acc[c][tt], a[tt], hv[c]);
         Ap += ns;
       }
+      const bool two = g.fx.n1 > 0;
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         if (cr[c] < 0) continue;
         float2* Ur = U + spad(cr[c] * st);
         const int t0 = tl.cols[tile * 4 + c].z;
+        if (two) {
+          // natural order t; the FFT applies the wave / centring factor while loading
+#pragma unroll
+          for (int tt = 0; tt < TS; ++tt)
+            if (tt < h.z) Ur[spad(t0 + tt)] = acc[c][tt];
+          continue;
+        }
         const int row = row0 + cr[c];
         const float2* py = g.post_y + (size_t)(row % g.ny) * g.ntx;
         const float2* pz = g.post_z + (size_t)(row / g.ny) * g.ntx;
@@ -250,7 +273,26 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
     __syncthreads();
     for (int r = 0; r < nrows; ++r) {
       float2* Ur = U + spad(r * st);
-      float2* R = fft_batch<+1, true>(Ur, B, os, nx, g.fx, tw, threadIdx.x, blockDim.x);
+      const float2* R;
+      if (g.fx.n1 > 0) {
+        const int row = row0 + r;
+        const float2* py = g.post_y + (size_t)(row % g.ny) * g.ntx;
+        const float2* pz = g.post_z + (size_t)(row / g.ny) * g.ntx;
+        auto ld = [&](int s, int m) {
+          const int t = m * os + s;
+          float2 pt = __ldg(py + t);
+          if (g.nz > 1) pt = cmul(pt, __ldg(pz + t));
+          return cmulc(pt, Ur[spad(t)]);
+        };
+        // the row's spectra are consumed by the first pass: the result
+        // overwrites them in natural order (transform s at s nx)
+        auto stf = [&](int s, int xx, float2 v) { Ur[s * nx + xx] = v; };
+        fft2p_cb_dispatch<+1>(g.fx.n1, g.fx.n2, ld, stf, B, os, tw, threadIdx.x, blockDim.x);
+        R = Ur;
+      } else {
+        R = fft_stockham<+1, true>(Ur, B, os, nx, g.fx, tw, threadIdx.x, blockDim.x);
+      }
+      const bool padr = g.fx.n1 == 0;
       const float2* crow = coil + n * L + (size_t)(row0 + r) * nx;
       // thread-owned output slots (r', x) = slot / nx, slot % nx
 #pragma unroll
@@ -259,7 +301,10 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
         if (slot < nrows * nx && slot / nx == r) {
           const int xx = slot - r * nx;
           float2 u = make_float2(0.f, 0.f);
-          for (int s = 0; s < os; ++s) cfmac(u, __ldg(g.pre + s * nx + xx), R[spad(s * nx + xx)]);
+          for (int s = 0; s < os; ++s) {
+            const int i = s * nx + xx;
+            cfmac(u, __ldg(g.pre + i), R[padr ? spad(i) : i]);
+          }
           cfmac(xacc[j], __ldg(crow + xx), u);
         }
       }
