@@ -217,9 +217,12 @@ def run_gpjc(args, rank, world, local):
     value = pairs_per_step * args.steps * world / (total_ms / 1e3)
 
     # ---- dominant kernel and its roofline (FP32 ALU bound)
-    names = {gpjc.STAGE_READOUT_FWD: "k1_fwd_fp32 (readout FFT + PSF + A_g)",
+    fp32 = prec == gpjc.FP32
+    names = {gpjc.STAGE_READOUT_FWD: ("k1f_tiled (coil x image, readout FFT, wave PSF, A_g)" if fp32 else
+                                      "k1_sim_fwd + k_tc_compress (16-bit spectra, tcgen05 A_g)"),
              gpjc.STAGE_PHASE_ENCODE: "k2 (phase-encode FFT / mask projection)",
-             gpjc.STAGE_READOUT_ADJ: "k1_adj_fp32 (A_g^H + inverse readout FFT + coil sum)"}
+             gpjc.STAGE_READOUT_ADJ: ("k1a_tiled (A_g^H, inverse readout FFT, coil sum)" if fp32 else
+                                      "k_tc_expand + k1_sim_adj (tcgen05 A_g^H, inverse FFT, coil sum)")}
     dom = max(prof, key=lambda s: prof[s][0])
     dom_ms = prof[dom][0] / max(prof[dom][1], 1)
     keep_avg = float(np.mean(g.keep))
