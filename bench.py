@@ -113,6 +113,12 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+# DRAM bytes (read + write) per launch of the readout kernels, from the ncu
+# capture summarised in profiles/k1_readout_2d256_fp32.md (stage -> bytes);
+# to be retaken whenever those kernels change.
+DRAM_TRAFFIC = {("2d256", 0): 22677248, ("2d256", 2): 30537216}
+
+
 def k1_flops(g, ntxc, keep_avg):
     """Algorithmic FP32 flops of one readout-stage launch (all rows, all
     coils): coil multiply (6 N_x), pre-twiddle (6 N_tx), os FFTs of N_x
@@ -230,8 +236,9 @@ def run_gpjc(args, rank, world, local):
     sm_mhz = clocks["sm_mhz"] or 2070.0
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled SM clock
     achieved = fl / (dom_ms * 1e-3) / 1e12
+    traffic = DRAM_TRAFFIC.get((wl.name, dom)) if fp32 else None
     roofline = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4), "traffic": traffic,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled SM clock)",
                 "launch_ms": round(dom_ms, 5),
                 "stage_share": {names[s]: round(prof[s][0] / max(total_ms, 1e-9), 4) for s in prof}}
