@@ -349,3 +349,24 @@ def test_3d_cg_end_to_end(gp):
     op = gp.Operator(grp, c_d)
     x, _ = op.recon(gp.compress(grp, to_dev(S)), alg=gp.CG, iters=wl.iters)
     assert O.nrmse(to_np(x), x_ref) < 1e-5
+
+
+# ------------------------------------------------------------ FFT lengths --
+
+@pytest.mark.parametrize("n", [40, 56, 160, 192, 224, 240, 288, 320])
+def test_two_pass_fft_lengths_match_oracle(gp, n):
+    """Every transform length with a two-pass plan (n = 8 x {5, 7} or
+    16 x {10, 12, 14, 15, 18, 20}) along both the readout and the
+    phase-encode axis: the uncompressed model, E_c and E_c^H against the
+    FP64 oracle."""
+    g = synth.tiny_geometry(nx=n, ny=n, nz=1, nc=2, os=2, cycles=2.0, kappa_y=1.9, n_groups=n // 8, keep=4,
+                            lines="regular", r=2)
+    coils, rho, roi = case_for(g, 30)
+    x = synth.complex_normal(g.shape, 31)
+    As, _, _ = O.build_groups(g, coils, roi)
+    plan = gp.Plan(g)
+    op = gp.Operator(gp.Groups.from_matrices(plan, As), to_dev(coils))
+    assert rel(to_np(op.simulate(to_dev(x))), O.E_apply(g, coils, x)) < 1e-5
+    assert rel(to_np(op.E(to_dev(x))), O.Ec_apply(g, coils, As, x)) < 1e-5
+    v = synth.complex_normal((g.n_lines, plan.ntx_c), 32)
+    assert rel(to_np(op.EH(to_dev(v))), O.EcH_apply(g, coils, As, v)) < 1e-5
