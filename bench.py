@@ -52,6 +52,33 @@ def dist_info():
     return rank, world, local
 
 
+# ---------------------------------------------------------------- ranks --
+def max_over_ranks(ms: float, world: int, dev) -> float:
+    """The slowest rank's time: the job is only as fast as its slowest
+    replica (all_reduce MAX over the process group; a no-op for one rank)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_step: float, steps: int, world: int, total_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (each rank runs its own slice: weak scaling)."""
+    return units_per_step * steps * world / (total_ms / 1e3)
+
+
+def rank_barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
 # ---------------------------------------------------------------- clocks --
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -185,8 +212,7 @@ def run_gpjc(args, rank, world, local):
     torch.cuda.synchronize()
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        rank_barrier(world)
 
     # ---- timed region (device events per step; L2 flushed between steps)
     sampler = ClockSampler(local)
@@ -214,13 +240,9 @@ def run_gpjc(args, rank, world, local):
     clocks = sampler.stop()
     op.profile(False)
     ms_steps = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(ms_steps)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ms_steps), world, dev)
     ms_per_step = total_ms / args.steps
-    value = pairs_per_step * args.steps * world / (total_ms / 1e3)
+    value = job_rate(pairs_per_step, args.steps, world, total_ms)
 
     # ---- dominant kernel and its roofline (FP32 ALU bound)
     fp32 = prec == gpjc.FP32
@@ -262,13 +284,9 @@ def run_gpjc(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        e2e_ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
         h2d = coils_h.numel() * 8 + roi_h.numel() + S_h.numel() * 8
-        e2e = {"value": round(pairs_per_step * e2e_steps * world / (e2e_ms / 1e3), 2), "unit": "pairs/s",
+        e2e = {"value": round(job_rate(pairs_per_step, e2e_steps, world, e2e_ms), 2), "unit": "pairs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(x_h.numel() * 8),
                "s_per_slice": round(e2e_ms / 1e3 / e2e_steps, 6)}
 
@@ -397,6 +415,10 @@ def run_batch(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
     wls = synth.batch_workloads(64)
     ops, scs, xs, keep = [], [], [], []
     gen = torch.Generator(device=dev).manual_seed(4)
@@ -428,6 +450,7 @@ def run_batch(args, rank, world, local):
     sampler.start()
     l0 = gpjc.launch_count()
     tot = 0.0
+    rank_barrier(world)
     for _ in range(args.steps):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -449,10 +472,12 @@ def run_batch(args, rank, world, local):
     e1.record(stream)
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1)
+    tot = max_over_ranks(tot, world, dev)
     ms = tot / args.steps
     pairs = len(ops) * iters
-    out = {"metric": METRIC + " (uneven 64-slice batch, CG-SENSE 30)", "value": round(pairs / (ms / 1e3), 2),
-           "unit": "pairs/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup),
+    out = {"metric": METRIC + " (uneven 64-slice batch, CG-SENSE 30)",
+           "value": round(job_rate(pairs, args.steps, world, tot), 2),
+           "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic",
            "config": {"workload": "batch64", "slices": len(ops), "iters": iters,
@@ -466,7 +491,10 @@ def run_batch(args, rank, world, local):
            "speedup_vs_sequential": round(seq_ms / ms, 3),
            "recon_s_per_slice": round(ms / 1e3 / len(ops), 6),
            "clocks": clocks, "gpu_launches": int(launches)}
-    print(json.dumps(out), flush=True)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 def main():
