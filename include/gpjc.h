@@ -109,7 +109,7 @@ typedef struct gpjc_build_params {
   int32_t eig_iters;      /* FP64 subspace iterations (0 = default: 1 after the FP32 phase, else 12) */
   int32_t block;          /* subspace block size b (0 = default: min(N_s, max(2 keep, keep + 16), 96)) */
   int32_t keep_gram;      /* keep P_g (FP64) for gpjc_groups_gram                             */
-  int32_t eig_iters_fp32; /* FP32 iterations before the FP64 ones (0 = default 10, -1 = none) */
+  int32_t eig_iters_fp32; /* FP32 iterations before the FP64 ones (0 = default 6, -1 = none)  */
 } gpjc_build_params;
 
 /* Builds every group's compression matrix from coil maps and a ROI

@@ -136,10 +136,21 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
       const int4 h = hdr[m];  // (aoff_g + k0, keep_g, kcnt, unused)
       if (h.z == 0) continue;
       const float2* Ap = AT + h.x + (size_t)nw * h.y;
+      // full tiles with 16-byte aligned rows take two 16-byte loads per tau
+      const bool vec = h.z == 4 && (h.y & 1) == 0 && (((uintptr_t)Ap) & 15) == 0;
       for (int tau = 0; tau < w; ++tau) {
         float2 a[4], u[4];
+        if (vec) {
+          const float4 a01 = __ldg(reinterpret_cast<const float4*>(Ap));
+          const float4 a23 = __ldg(reinterpret_cast<const float4*>(Ap + 2));
+          a[0] = make_float2(a01.x, a01.y);
+          a[1] = make_float2(a01.z, a01.w);
+          a[2] = make_float2(a23.x, a23.y);
+          a[3] = make_float2(a23.z, a23.w);
+        } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) a[k] = k < h.z ? __ldg(Ap + k) : make_float2(0.f, 0.f);
+          for (int k = 0; k < 4; ++k) a[k] = k < h.z ? __ldg(Ap + k) : make_float2(0.f, 0.f);
+        }
 #pragma unroll
         for (int c = 0; c < 4; ++c) u[c] = uoff[m][c] >= 0 ? U[spad(uoff[m][c] + tau)] : make_float2(0.f, 0.f);
 #pragma unroll
@@ -226,10 +237,21 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
 #pragma unroll
         for (int k = 0; k < TS; ++k) acc[c][k] = make_float2(0.f, 0.f);
       const float2* Ap = Arow + h.x + n * w;
+      // full tiles with 16-byte aligned rows load two samples at a time
+      const bool vec = h.z == TS && (ns & 1) == 0 && (((uintptr_t)Ap) & 15) == 0;
       for (int k = 0; k < h.y; ++k) {
         float2 a[TS], hv[4];
+        if (vec) {
 #pragma unroll
-        for (int tt = 0; tt < TS; ++tt) a[tt] = tt < h.z ? __ldg(Ap + tt) : make_float2(0.f, 0.f);
+          for (int tt = 0; tt < TS; tt += 2) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(Ap + tt));
+            a[tt] = make_float2(v.x, v.y);
+            a[tt + 1] = make_float2(v.z, v.w);
+          }
+        } else {
+#pragma unroll
+          for (int tt = 0; tt < TS; ++tt) a[tt] = tt < h.z ? __ldg(Ap + tt) : make_float2(0.f, 0.f);
+        }
         if (hs) {
 #pragma unroll
           for (int c = 0; c < 4; ++c) hv[c] = cr[c] >= 0 ? Hs[hpad(hoff[c] + k)] : make_float2(0.f, 0.f);
