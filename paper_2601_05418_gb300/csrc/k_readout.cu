@@ -25,9 +25,15 @@ constexpr int kRThreads = 256;
 // row's padded sub-buffer starts at spad(r * stride))
 __host__ __device__ inline int u_stride(int ntx) { return (ntx + 7) & ~7; }
 
+// forward spectra U: two padding values every 8, so that a patch of 8 (or
+// 16, ...) samples starts on a 16-byte boundary and pairs of samples can be
+// read with one 16-byte load
+__host__ __device__ inline int upad(int i) { return i + 2 * (i >> 3); }
+__host__ __device__ inline int upad_size(int n) { return n + 2 * (n >> 3) + 2; }
+
 size_t readout_fwd_smem(const Geo& g, int rb) {
   const int st = u_stride(g.ntx);
-  return sizeof(float2) * (size_t)(spad_size(rb * st) + 2 * spad_size(g.ntx) + g.nx);
+  return sizeof(float2) * (size_t)(upad_size(rb * st) + 2 * spad_size(g.ntx) + g.nx);
 }
 // staged H2 rows: one padding slot every 16 columns (conflict-free when the
 // tiles of a warp read columns 16 kept components apart)
@@ -64,7 +70,7 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
                                          float2* rsm) {
   const int rb = tl.rb, st = u_stride(g.ntx);
   float2* U = rsm;
-  float2* A = U + spad_size(rb * st);
+  float2* A = U + upad_size(rb * st);
   float2* B = A + spad_size(g.ntx);
   float2* tw = B + spad_size(g.ntx);
   const int row0 = rblock * rb;
@@ -96,7 +102,7 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
       const int row = row0 + r;
       const float2* crow = coil + n * L + (size_t)row * nx;
       const float2* xrow = x + (size_t)row * nx;
-      float2* Ur = U + spad(r * st);
+      float2* Ur = U + upad(r * st);
       const float2* py = g.post_y + (size_t)(row % g.ny) * g.ntx;
       const float2* pz = g.post_z + (size_t)(row / g.ny) * g.ntx;
       if (g.fx.n1 > 0) {
@@ -109,7 +115,7 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
           const int t = m * os + s;
           float2 pt = __ldg(py + t);
           if (g.nz > 1) pt = cmul(pt, __ldg(pz + t));
-          Ur[spad(t)] = cmul(v, pt);
+          Ur[upad(t)] = cmul(v, pt);
         };
         fft2p_cb_dispatch<-1>(g.fx.n1, g.fx.n2, ld, stf, B, os, tw, threadIdx.x, blockDim.x);
       } else {
@@ -125,7 +131,7 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
             const int t = m * os + s;
             float2 pt = __ldg(py + t);
             if (g.nz > 1) pt = cmul(pt, __ldg(pz + t));
-            Ur[spad(t)] = cmul(R[spad(s * nx + m)], pt);
+            Ur[upad(t)] = cmul(R[spad(s * nx + m)], pt);
           }
         __syncthreads();
       }
@@ -138,6 +144,41 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
       const float2* Ap = AT + h.x + (size_t)nw * h.y;
       // full tiles with 16-byte aligned rows take two 16-byte loads per tau
       const bool vec = h.z == 4 && (h.y & 1) == 0 && (((uintptr_t)Ap) & 15) == 0;
+      // patches on 8-sample boundaries: two samples per 16-byte load of U
+      bool upair = vec && (w & 7) == 0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) upair = upair && (uoff[m][c] < 0 || (uoff[m][c] & 7) == 0);
+      if (upair) {
+        for (int tau = 0; tau < w; tau += 2) {
+          float2 a0[4], a1[4], u0[4], u1[4];
+          {
+            const float4 p01 = __ldg(reinterpret_cast<const float4*>(Ap));
+            const float4 p23 = __ldg(reinterpret_cast<const float4*>(Ap + 2));
+            const float4 q01 = __ldg(reinterpret_cast<const float4*>(Ap + h.y));
+            const float4 q23 = __ldg(reinterpret_cast<const float4*>(Ap + h.y + 2));
+            a0[0] = make_float2(p01.x, p01.y); a0[1] = make_float2(p01.z, p01.w);
+            a0[2] = make_float2(p23.x, p23.y); a0[3] = make_float2(p23.z, p23.w);
+            a1[0] = make_float2(q01.x, q01.y); a1[1] = make_float2(q01.z, q01.w);
+            a1[2] = make_float2(q23.x, q23.y); a1[3] = make_float2(q23.z, q23.w);
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (uoff[m][c] >= 0) v = *reinterpret_cast<const float4*>(U + upad(uoff[m][c] + tau));
+            u0[c] = make_float2(v.x, v.y);
+            u1[c] = make_float2(v.z, v.w);
+          }
+#pragma unroll
+          for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              cfma(acc[m][c][k], a0[k], u0[c]);
+              cfma(acc[m][c][k], a1[k], u1[c]);
+            }
+          Ap += 2 * h.y;
+        }
+        continue;
+      }
       for (int tau = 0; tau < w; ++tau) {
         float2 a[4], u[4];
         if (vec) {
@@ -152,7 +193,7 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
           for (int k = 0; k < 4; ++k) a[k] = k < h.z ? __ldg(Ap + k) : make_float2(0.f, 0.f);
         }
 #pragma unroll
-        for (int c = 0; c < 4; ++c) u[c] = uoff[m][c] >= 0 ? U[spad(uoff[m][c] + tau)] : make_float2(0.f, 0.f);
+        for (int c = 0; c < 4; ++c) u[c] = uoff[m][c] >= 0 ? U[upad(uoff[m][c] + tau)] : make_float2(0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
