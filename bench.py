@@ -140,10 +140,11 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# DRAM bytes (read + write) per launch of the readout kernels, from the ncu
-# capture summarised in profiles/k1_readout_2d256_fp32.md (stage -> bytes);
-# to be retaken whenever those kernels change.
-DRAM_TRAFFIC = {("2d256", 0): 22677248, ("2d256", 2): 30537216}
+# DRAM bytes (read + write) per launch of the adjoint readout kernel, from
+# the ncu capture summarised in profiles/k1_readout_2d256_fp32.md; to be
+# retaken whenever that kernel changes.  (The forward kernel's traffic
+# depends on the autotuned coil-chunk count, so it is not recorded.)
+DRAM_TRAFFIC = {("2d256", 2): 30536448}
 
 
 def k1_flops(g, ntxc, keep_avg):
