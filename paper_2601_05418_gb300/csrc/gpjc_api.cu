@@ -709,6 +709,7 @@ struct gpjc_op {
   gpjc_precision prec;
   int nchunk, nchunk_max;      // coil chunks of the forward readout (partial Hpart planes)
   int nchunk_a, nchunk_a_max;  // coil chunks of the adjoint readout (partial images in xparts)
+  int adj_pieces;             // 16-bit operators: row pieces of the adjoint readout (V stays in L2)
   size_t L;
   float2 *Hpart, *T, *H2, *xparts;
   float2 *vb, *vr, *vp, *vy, *vv, *vtmp;
@@ -766,6 +767,17 @@ static int auto_nchunk_adj(const gpjc_plan* p) {
   return n;
 }
 
+// 16-bit operators: the adjoint expands A_g^H H into FP32 spectra
+// [rows][nc][ntx] before the inverse readout FFT; in row pieces of at most
+// ~40 MB of spectra each, the spectra are read back from L2 instead of HBM
+constexpr int kMaxAdjPieces = 8;
+static int auto_adj_pieces(const gpjc_plan* p) {
+  const double bytes = 8.0 * p->ny * p->nz * p->nc * p->os * p->nx;
+  int n = 1;
+  while (bytes / n > 40e6 && n < kMaxAdjPieces) n *= 2;
+  return n;
+}
+
 static int auto_nchunk(const gpjc_plan* p) {
   const int rows = p->ny * p->nz;
   int n = 1;
@@ -808,6 +820,7 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
     while (n * 2 <= p->nc && (size_t)n * 2 * op->L * sizeof(float2) <= ((size_t)1 << 30)) n *= 2;
     op->nchunk_a_max = std::max(n, nmax);
     op->nchunk_a = std::min(auto_nchunk_adj(p), op->nchunk_a_max);
+    op->adj_pieces = auto_adj_pieces(p);
   }
   const size_t HN = (size_t)g.rows * g.ntxc;
   gpjc_status s;
@@ -892,10 +905,19 @@ static cudaError_t readout_adj(const gpjc_op* op, cudaStream_t st) {
     const int fmt = op->prec == GPJC_BF16 ? 1 : 0;
     TcGeom t = p->tc16;
     t.scale = op->gr->scale;
-    cudaError_t e =
-        launch_tc_expand(t, fmt, op->H2, op->gr->tc_bx[fmt], (float2*)op->V16, p->geo.rows, op->status, st);
-    if (e != cudaSuccess) return e;
-    return launch_sim_adj(p->geo, (const float2*)op->V16, op->coil, op->xparts, op->nchunk_a, st);
+    const Geo& g = p->geo;
+    // pieces of whole expansion row tiles
+    const int tiles = (g.rows + t.lt - 1) / t.lt;
+    const int per = (tiles + op->adj_pieces - 1) / op->adj_pieces * t.lt;
+    for (int r0 = 0; r0 < g.rows; r0 += per) {
+      const int nr = std::min(per, g.rows - r0);
+      cudaError_t e = launch_tc_expand(t, fmt, op->H2 + (size_t)r0 * g.ntxc, op->gr->tc_bx[fmt],
+                                       (float2*)op->V16 + (size_t)r0 * g.nc * g.ntx, nr, op->status, st);
+      if (e != cudaSuccess) return e;
+      e = launch_sim_adj_rows(g, (const float2*)op->V16, op->coil, op->xparts, op->nchunk_a, r0, nr, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
   if (p->rt_a.rb && !op->legacy_readout)
     return launch_k1a_tiled(p->geo, p->rt_a, op->H2, op->coil, op->gr->A, op->xparts, op->nchunk_a, st);
@@ -1032,12 +1054,14 @@ extern "C" gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchu
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  const int keep_f = op->nchunk, keep_a = op->nchunk_a;
+  const int keep_f = op->nchunk, keep_a = op->nchunk_a, keep_p = op->adj_pieces;
   gpjc_status s = GPJC_OK;
-  // adjoint chunks first (forward fixed), then forward chunks
-  for (int pass = 0; pass < 2 && !s; ++pass) {
-    int* knob = pass == 0 ? &op->nchunk_a : &op->nchunk;
-    const int nmax = pass == 0 ? op->nchunk_a_max : op->nchunk_max;
+  // adjoint chunks first (forward fixed), then forward chunks, then (16-bit
+  // operators) the row pieces of the adjoint
+  const int npass = op->prec == GPJC_FP32 ? 2 : 3;
+  for (int pass = 0; pass < npass && !s; ++pass) {
+    int* knob = pass == 0 ? &op->nchunk_a : pass == 1 ? &op->nchunk : &op->adj_pieces;
+    const int nmax = pass == 0 ? op->nchunk_a_max : pass == 1 ? op->nchunk_max : kMaxAdjPieces;
     float best = 1e30f;
     int best_n = *knob;
     for (int n = 1; n <= nmax && !s; n *= 2) {
@@ -1056,6 +1080,7 @@ extern "C" gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchu
   if (s) {
     op->nchunk = keep_f;
     op->nchunk_a = keep_a;
+    op->adj_pieces = keep_p;
     return s;
   }
   if (op->gexec) {
@@ -1146,12 +1171,13 @@ extern "C" gpjc_status gpjc_recon(const gpjc_op* cop, const float* d_Sc, float* 
   cudaStream_t st = (cudaStream_t)stream;
   gpjc_status s;
   if (rp.use_graph) {
-    std::vector<char> key(sizeof(rp) + 2 * sizeof(void*) + 2 * sizeof(int));
+    std::vector<char> key(sizeof(rp) + 2 * sizeof(void*) + 3 * sizeof(int));
     memcpy(key.data(), &rp, sizeof(rp));
     memcpy(key.data() + sizeof(rp), &d_Sc, sizeof(void*));
     memcpy(key.data() + sizeof(rp) + sizeof(void*), &d_x, sizeof(void*));
     memcpy(key.data() + sizeof(rp) + 2 * sizeof(void*), &op->nchunk, sizeof(int));
     memcpy(key.data() + sizeof(rp) + 2 * sizeof(void*) + sizeof(int), &op->nchunk_a, sizeof(int));
+    memcpy(key.data() + sizeof(rp) + 2 * sizeof(void*) + 2 * sizeof(int), &op->adj_pieces, sizeof(int));
     cudaStream_t cs = op->cap_st;
     CK(cudaEventRecord(op->ev_in, st));
     CK(cudaStreamWaitEvent(cs, op->ev_in, 0));

@@ -26,6 +26,9 @@ cudaError_t launch_sim_fwd_bf16(const Geo& g, const float2* x, const float2* coi
                                 cudaStream_t st);
 cudaError_t launch_sim_adj(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
                            cudaStream_t st);
+// rows [row0, row0 + nrows) only (the other rows' partial images are untouched)
+cudaError_t launch_sim_adj_rows(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
+                                int row0, int nrows, cudaStream_t st);
 cudaError_t launch_sim_adj_bf16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,
                                 cudaStream_t st);
 cudaError_t launch_pe_fwd(const Geo& g, const float2* Hpart, int nchunk, int ncols, float2* T, float2* Sc,

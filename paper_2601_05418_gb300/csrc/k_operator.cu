@@ -198,122 +198,6 @@ __global__ void __launch_bounds__(kK1Threads) k1_adj_fp32(Geo g, const float2* _
 }
 
 // -------------------------------------------------------------------------
-// Uncompressed readout stage (the acquisition model E, and the first half of
-// the BF16 operator): V[row][n][t] = Psi F_ro (c_n x) for each coil.
-template <typename VT>
-__device__ __forceinline__ void store_v(VT* p, float2 v);
-template <>
-__device__ __forceinline__ void store_v<float2>(float2* p, float2 v) { *p = v; }
-template <>
-__device__ __forceinline__ void store_v<__nv_bfloat162>(__nv_bfloat162* p, float2 v) {
-  *p = __floats2bfloat162_rn(v.x, v.y);
-}
-template <>
-__device__ __forceinline__ void store_v<__half2>(__half2* p, float2 v) {
-  *p = __floats2half2_rn(v.x, v.y);
-}
-template <typename VT>
-__device__ __forceinline__ float2 load_v(const VT* p);
-template <>
-__device__ __forceinline__ float2 load_v<__half2>(const __half2* p) {
-  return __half22float2(*p);
-}
-template <>
-__device__ __forceinline__ float2 load_v<float2>(const float2* p) { return *p; }
-template <>
-__device__ __forceinline__ float2 load_v<__nv_bfloat162>(const __nv_bfloat162* p) {
-  return __bfloat1622float2(*p);
-}
-
-// smem: two padded ntx buffers + twiddles; post / pre are read from their
-// global tables (L2 / L1 resident) in coalesced order
-static size_t sim_smem(const Geo& g) { return sizeof(float2) * (size_t)(2 * spad_size(g.ntx) + g.nx); }
-
-__device__ __forceinline__ float2 post_of(const Geo& g, int t, int row) {
-  const int y = row % g.ny, z = row / g.ny;
-  const float2 py = __ldg(g.post_y + (size_t)y * g.ntx + t);
-  if (g.nz == 1) return py;
-  return cmul(py, __ldg(g.post_z + (size_t)z * g.ntx + t));
-}
-
-template <typename VT>
-__global__ void __launch_bounds__(kK1Threads) k1_sim_fwd(Geo g, const float2* __restrict__ x,
-                                                         const float2* __restrict__ coil,
-                                                         VT* __restrict__ V, int cpc) {
-  extern __shared__ float2 smem[];
-  float2* A = smem;
-  float2* B = A + spad_size(g.ntx);
-  float2* tw = B + spad_size(g.ntx);
-  const int row = blockIdx.x, chunk = blockIdx.y;
-  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) tw[i] = g.tw_x[i];
-  const size_t L = (size_t)g.rows * g.nx;
-  const int nx = g.nx, os = g.os;
-  const float2* xrow = x + (size_t)row * nx;
-  const int n0 = chunk * cpc;
-  const int n1 = min(g.nc, n0 + cpc);
-  for (int n = n0; n < n1; ++n) {
-    const float2* crow = coil + n * L + (size_t)row * nx;
-    for (int i = threadIdx.x; i < g.ntx; i += blockDim.x) {
-      const int xx = i % nx;
-      A[spad(i)] = cmul(cmul(__ldg(crow + xx), __ldg(xrow + xx)), __ldg(g.pre + i));
-    }
-    __syncthreads();
-    const float2* R = fft_batch<-1, true>(A, B, os, nx, g.fx, tw, threadIdx.x, blockDim.x);
-    VT* out = V + ((size_t)row * g.nc + n) * g.ntx;
-    for (int t = threadIdx.x; t < g.ntx; t += blockDim.x) {
-      const int m = t / os, s = t - m * os;
-      store_v<VT>(out + t, cmul(R[spad(s * nx + m)], post_of(g, t, row)));
-    }
-    __syncthreads();
-  }
-}
-
-template <typename VT, int MAXX>
-__global__ void __launch_bounds__(kK1Threads) k1_sim_adj(Geo g, const VT* __restrict__ V,
-                                                         const float2* __restrict__ coil,
-                                                         float2* __restrict__ xpart, int cpc) {
-  extern __shared__ float2 smem[];
-  float2* A = smem;
-  float2* B = A + spad_size(g.ntx);
-  float2* tw = B + spad_size(g.ntx);
-  const int row = blockIdx.x, chunk = blockIdx.y;
-  for (int i = threadIdx.x; i < g.nx; i += blockDim.x) tw[i] = g.tw_x[i];
-  const size_t L = (size_t)g.rows * g.nx;
-  const int nx = g.nx, os = g.os;
-  float2 xacc[MAXX];
-#pragma unroll
-  for (int j = 0; j < MAXX; ++j) xacc[j] = make_float2(0.f, 0.f);
-  const int n0 = chunk * cpc;
-  const int n1 = min(g.nc, n0 + cpc);
-  for (int n = n0; n < n1; ++n) {
-    const VT* vin = V + ((size_t)row * g.nc + n) * g.ntx;
-    for (int t = threadIdx.x; t < g.ntx; t += blockDim.x) {
-      const int m = t / os, s = t - m * os;
-      A[spad(s * nx + m)] = cmulc(post_of(g, t, row), load_v<VT>(vin + t));
-    }
-    __syncthreads();
-    const float2* R = fft_batch<+1, true>(A, B, os, nx, g.fx, tw, threadIdx.x, blockDim.x);
-    const float2* crow = coil + n * L + (size_t)row * nx;
-#pragma unroll
-    for (int j = 0; j < MAXX; ++j) {
-      const int xx = threadIdx.x + j * kK1Threads;
-      if (xx < nx) {
-        float2 u = make_float2(0.f, 0.f);
-        for (int s = 0; s < os; ++s) cfmac(u, __ldg(g.pre + s * nx + xx), R[spad(s * nx + xx)]);
-        cfmac(xacc[j], __ldg(crow + xx), u);
-      }
-    }
-    __syncthreads();
-  }
-  float2* out = xpart + ((size_t)chunk * g.rows + row) * nx;
-#pragma unroll
-  for (int j = 0; j < MAXX; ++j) {
-    const int xx = threadIdx.x + j * kK1Threads;
-    if (xx < nx) out[xx] = xacc[j];
-  }
-}
-
-// -------------------------------------------------------------------------
 // Phase-encode stage.  H is [rows][ncols]; a block owns kCB columns.
 // Centred unitary DFT along y: F[ky,y] = (-1)^{y} (-1)^{ky + ny/2}
 // exp(-2 pi i ky y / ny) / sqrt(ny).
@@ -546,58 +430,6 @@ cudaError_t launch_k1_adj_fp32(const Geo& g, const float2* H2, const float2* coi
   if (need <= 2) K1A(2)
 #undef K1A
   return cudaErrorInvalidValue;
-}
-
-template <typename VT>
-static cudaError_t launch_sim_fwd_t(const Geo& g, const float2* x, const float2* coil, VT* V, int nchunk,
-                                    cudaStream_t st) {
-  const int cpc = (g.nc + nchunk - 1) / nchunk;
-  dim3 grid(g.rows, nchunk);
-  const size_t sm = sim_smem(g);
-  cudaFuncSetAttribute(k1_sim_fwd<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  note_launches(1); k1_sim_fwd<VT><<<grid, kK1Threads, sm, st>>>(g, x, coil, V, cpc);
-  return cudaGetLastError();
-}
-
-template <typename VT>
-static cudaError_t launch_sim_adj_t(const Geo& g, const VT* V, const float2* coil, float2* xpart, int nchunk,
-                                    cudaStream_t st) {
-  const int cpc = (g.nc + nchunk - 1) / nchunk;
-  dim3 grid(g.rows, nchunk);
-  const size_t sm = sim_smem(g);
-  if (g.nx <= kK1Threads) {
-    cudaFuncSetAttribute(k1_sim_adj<VT, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    note_launches(1); k1_sim_adj<VT, 1><<<grid, kK1Threads, sm, st>>>(g, V, coil, xpart, cpc);
-  } else {
-    cudaFuncSetAttribute(k1_sim_adj<VT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    note_launches(1); k1_sim_adj<VT, 2><<<grid, kK1Threads, sm, st>>>(g, V, coil, xpart, cpc);
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_sim_fwd(const Geo& g, const float2* x, const float2* coil, float2* V, int nchunk,
-                           cudaStream_t st) {
-  return launch_sim_fwd_t<float2>(g, x, coil, V, nchunk, st);
-}
-cudaError_t launch_sim_fwd_bf16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
-                                cudaStream_t st) {
-  return launch_sim_fwd_t<__nv_bfloat162>(g, x, coil, (__nv_bfloat162*)V, nchunk, st);
-}
-cudaError_t launch_sim_fwd_f16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
-                               cudaStream_t st) {
-  return launch_sim_fwd_t<__half2>(g, x, coil, (__half2*)V, nchunk, st);
-}
-cudaError_t launch_sim_adj_f16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,
-                               cudaStream_t st) {
-  return launch_sim_adj_t<__half2>(g, (const __half2*)V, coil, xpart, nchunk, st);
-}
-cudaError_t launch_sim_adj(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
-                           cudaStream_t st) {
-  return launch_sim_adj_t<float2>(g, V, coil, xpart, nchunk, st);
-}
-cudaError_t launch_sim_adj_bf16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,
-                                cudaStream_t st) {
-  return launch_sim_adj_t<__nv_bfloat162>(g, (const __nv_bfloat162*)V, coil, xpart, nchunk, st);
 }
 
 static void set_k2_attr(const void* f, size_t sm) {
