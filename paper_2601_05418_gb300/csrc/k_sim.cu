@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(kK1Threads) k1_sim_adj2(Geo g, const VT* __res
 
 constexpr size_t kSimSmemMax = 200 * 1024;
 
-// GPJC_SIM_LEGACY=1 keeps the one-coil kernels on two-pass lengths too
+// GPJC_SIM_LEGACY=1 keeps the one-coil kernels on two-pass lengths too (on the
+// 256 x 256, 32-coil BF16 FISTA step the two-coil forward saved 2 ms of 43,
+// the two-coil adjoint 0.25 ms of 39)
 static bool sim_two_pass(const Geo& g) {
   static int legacy = -1;
   if (legacy < 0) {
@@ -255,17 +257,6 @@ static bool sim_two_pass(const Geo& g) {
     legacy = (e && e[0] == '1') ? 1 : 0;
   }
   return !legacy && g.fx.n1 > 0 && sim2_smem<2>(g) <= kSimSmemMax;
-}
-
-// GPJC_SIM_ADJ2=1 selects the two-coil adjoint kernel (the one-coil kernel
-// holds more blocks per SM)
-static bool sim_adj_two_coil() {
-  static int on = -1;
-  if (on < 0) {
-    const char* e = getenv("GPJC_SIM_ADJ2");
-    on = (e && e[0] == '1') ? 1 : 0;
-  }
-  return on == 1;
 }
 
 template <typename VT, int NB>
@@ -306,7 +297,7 @@ static cudaError_t launch_sim_adj_t(const Geo& g, const VT* V, const float2* coi
   dim3 grid(nrows, nchunk);
   // (FP32 spectra only: the adjoint of the 16-bit operators expands into FP32)
   if constexpr (std::is_same<VT, float2>::value)
-    if (sim_adj_two_coil() && sim_two_pass(g))
+    if (sim_two_pass(g))
       return g.nx <= kK1Threads ? launch_sim_adj2<VT, 2, 1>(g, V, coil, xpart, cpc, grid, row0, st)
                                 : launch_sim_adj2<VT, 2, 2>(g, V, coil, xpart, cpc, grid, row0, st);
   const size_t sm = sim_smem(g);

@@ -426,10 +426,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
     for (int col = 0; col < nrows; col += 8) {
       float v[8];
       tmem_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col, v);
-      if (valid) {
+      const int i0 = (nt * 256 + col) / 2;  // patch vector index n w + tau of v[0], a multiple of 4
+      if (valid && (t.w & 3) == 0) {
+        // the four samples share the coil n and start on a 32-byte boundary
+        if (i0 < t.ns) {
+          const int n = i0 / t.w, tau = i0 - n * t.w;
+          float4* dst = reinterpret_cast<float4*>(V + ((size_t)row * t.nc + n) * t.ntx + p * t.w + tau);
+          dst[0] = make_float4(v[0] * s, v[1] * s, v[2] * s, v[3] * s);
+          dst[1] = make_float4(v[4] * s, v[5] * s, v[6] * s, v[7] * s);
+        }
+      } else if (valid) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int i = (nt * 256 + col) / 2 + j;  // patch vector index n w + tau
+          const int i = i0 + j;
           if (i < t.ns) {
             const int n = i / t.w, tau = i - n * t.w;
             V[((size_t)row * t.nc + n) * t.ntx + p * t.w + tau] = make_float2(v[2 * j] * s, v[2 * j + 1] * s);
