@@ -821,6 +821,12 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
     op->nchunk_a_max = std::max(n, nmax);
     op->nchunk_a = std::min(auto_nchunk_adj(p), op->nchunk_a_max);
     op->adj_pieces = auto_adj_pieces(p);
+    // GPJC_ADJ_PIECES=n (1..8) overrides the default split (the results do
+    // not depend on it: whole expansion row tiles per piece)
+    if (const char* e = getenv("GPJC_ADJ_PIECES")) {
+      const int v = atoi(e);
+      if (v >= 1 && v <= kMaxAdjPieces) op->adj_pieces = v;
+    }
   }
   const size_t HN = (size_t)g.rows * g.ntxc;
   gpjc_status s;
