@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default="2d256", choices=["2d256", "2d256h", "2d256bf", "2d128", "batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the BF16 tensor-core step timed beside the FP32 one (2d256)")
     return ap.parse_args()
 
 
@@ -248,10 +250,10 @@ def run_gpjc(args, rank, world, local):
     # ---- dominant kernel and its roofline (FP32 ALU bound)
     fp32 = prec == gpjc.FP32
     names = {gpjc.STAGE_READOUT_FWD: ("k1f_tiled (coil x image, readout FFT, wave PSF, A_g)" if fp32 else
-                                      "k1_sim_fwd + k_tc_compress (16-bit spectra, tcgen05 A_g)"),
+                                      "k1_sim_fwd2 + k_tc_compress (16-bit spectra, tcgen05 A_g)"),
              gpjc.STAGE_PHASE_ENCODE: "k2 (phase-encode FFT / mask projection)",
              gpjc.STAGE_READOUT_ADJ: ("k1a_tiled (A_g^H, inverse readout FFT, coil sum)" if fp32 else
-                                      "k_tc_expand + k1_sim_adj (tcgen05 A_g^H, inverse FFT, coil sum)")}
+                                      "k_tc_expand + k1_sim_adj2 (tcgen05 A_g^H, inverse FFT, coil sum)")}
     dom = max(prof, key=lambda s: prof[s][0])
     dom_ms = prof[dom][0] / max(prof[dom][1], 1)
     keep_avg = float(np.mean(g.keep))
@@ -291,6 +293,48 @@ def run_gpjc(args, rank, world, local):
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(x_h.numel() * 8),
                "s_per_slice": round(e2e_ms / 1e3 / e2e_steps, 6)}
 
+    # ---- the same step with the BF16 tensor-core operator, timed the same
+    # way: the metric compares it with the plain FP32 step
+    bf16 = None
+    if fp32 and wl.name == "2d256" and not args.no_compare:
+        x32 = x.clone()
+        op16 = gpjc.Operator(grp, coils, gpjc.BF16)
+        op16.autotune()
+        op16.profile(True)  # the same stage events as the FP32 step, so the two times compare like for like
+        Sc16 = torch.empty_like(Sc)
+        x16 = torch.empty_like(x)
+
+        def step16():
+            grp.rebuild(coils, roi)
+            gpjc.compress(grp, S, gpjc.BF16, out=Sc16)
+            op16.recon(Sc16, alg=gpjc.FISTA, iters=wl.iters, lam=wl.lam, power_iters=power_iters,
+                       haar_levels=wl.haar_levels, out=x16, sync=False)
+
+        for _ in range(max(3, args.warmup)):
+            step16()
+        torch.cuda.synchronize()
+        barrier()
+        ev16 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.zero_()
+            ev16[i][0].record(stream)
+            step16()
+            ev16[i][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        op16.profile(False)
+        ms16 = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev16), world, dev)
+        v16 = job_rate(pairs_per_step, args.steps, world, ms16)
+        # NRMSE (complex, full grid) of the BF16 image against this run's FP32 image
+        ref_abs = x32.abs()
+        nr = float((x16 - x32).abs().pow(2).mean().sqrt() / (ref_abs.max() - ref_abs.min()))
+        bf16 = {"dtype": "bf16", "value": round(v16, 2), "unit": "pairs/s",
+                "ms_per_step": round(ms16 / args.steps, 4), "speedup_vs_fp32": round(v16 / value, 3),
+                "nrmse_vs_fp32_image": float(f"{nr:.3e}"),
+                "note": "same workload, inputs, stage events and timing as the FP32 step; NRMSE against "
+                        "the FP64 oracle is checked by the tests"}
+
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
@@ -309,6 +353,8 @@ def run_gpjc(args, rank, world, local):
         "gpu_launches": int(launches),
         "e2e": e2e,
     }
+    if bf16 is not None:
+        out["bf16_tensor_core_step"] = bf16
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, pairs_per_step, power_iters)
     if rank == 0:
