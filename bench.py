@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--workload", default="2d256", choices=["2d256", "2d256h", "2d256bf", "2d128", "batch64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--torch-floor", action="store_true",
+                    help="time the plain-PyTorch FP32 operator beside the library's (2D workloads)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the BF16 tensor-core step timed beside the FP32 one (2d256)")
     return ap.parse_args()
@@ -544,6 +546,114 @@ def run_batch(args, rank, world, local):
         torch.distributed.destroy_process_group()
 
 
+# ---------------------------------------------------------- torch floor --
+class TorchFloor:
+    """Plain-PyTorch FP32 E_c and E_c^H of a 2D slice (torch.fft and complex64
+    batched matmul), the sanity floor the hand-written kernels are compared
+    with; not part of the library.  Same model and conventions as the
+    library (Eq. 1-4, 13-15): coil multiply, centred zero-padded unitary
+    readout DFT, wave phase exp(-i 2 pi a_y(t) y_c / N_y), patch compression
+    by A_{g(p)} on the coil-major patch vector (n w + tau), centred unitary
+    phase-encode DFT, line gather.  The group map may be any, the kept
+    dimension must be the same for every group."""
+
+    def __init__(self, g, coils, As, dev):
+        import numpy as np
+        import torch
+
+        assert g.nz == 1, "2D slices only"
+        keep = {int(k) for k in g.keep}
+        assert len(keep) == 1, "uniform kept dimension"
+        self.g, self.k = g, keep.pop()
+        self.np_ = g.ntx // g.w
+        t = np.arange(g.ntx, dtype=np.float64)
+        ay = g.kappa_y * (1 - np.cos(2 * np.pi * g.cycles * t / g.ntx)) / 2
+        yc = (np.arange(g.ny) - g.ny // 2) / g.ny
+        self.psf = torch.from_numpy(np.exp(-2j * np.pi * yc[:, None] * ay[None, :]).astype(np.complex64)).to(dev)
+        self.coils = torch.as_tensor(coils).to(dev, torch.complex64).reshape(g.nc, g.ny, g.nx)
+        self.Ap = torch.from_numpy(np.stack([np.asarray(As[int(q)]) for q in g.patch_group]).astype(np.complex64)).to(dev)
+        self.lines = torch.as_tensor(np.asarray(g.line_ky, dtype=np.int64)).to(dev)
+        self.s0 = g.ntx // 2 - g.nx // 2
+
+    def E(self, rho):
+        import torch
+
+        g, fft = self.g, torch.fft
+        U = torch.zeros((g.nc, g.ny, g.ntx), dtype=torch.complex64, device=rho.device)
+        U[..., self.s0:self.s0 + g.nx] = self.coils * rho.reshape(1, g.ny, g.nx)
+        U = fft.fftshift(fft.fft(fft.ifftshift(U, dim=-1), dim=-1, norm="ortho"), dim=-1) * self.psf
+        V = U.reshape(g.nc, g.ny, self.np_, g.w).permute(1, 2, 0, 3).reshape(g.ny, self.np_, g.nc * g.w)
+        H = torch.einsum("pki,ypi->ypk", self.Ap, V).reshape(g.ny, self.np_ * self.k)
+        K = fft.fftshift(fft.fft(fft.ifftshift(H, dim=0), dim=0, norm="ortho"), dim=0)
+        return K[self.lines]
+
+    def EH(self, Sc):
+        import torch
+
+        g, fft = self.g, torch.fft
+        K = torch.zeros((g.ny, self.np_ * self.k), dtype=torch.complex64, device=Sc.device)
+        K[self.lines] = Sc
+        H = fft.fftshift(fft.ifft(fft.ifftshift(K, dim=0), dim=0, norm="ortho"), dim=0)
+        V = torch.einsum("pki,ypk->ypi", self.Ap.conj(), H.reshape(g.ny, self.np_, self.k))
+        U = V.reshape(g.ny, self.np_, g.nc, g.w).permute(2, 0, 1, 3).reshape(g.nc, g.ny, g.ntx) * self.psf.conj()
+        u = fft.fftshift(fft.ifft(fft.ifftshift(U, dim=-1), dim=-1, norm="ortho"), dim=-1)
+        return (self.coils.conj() * u[..., self.s0:self.s0 + g.nx]).sum(0).reshape(1, g.ny, g.nx)
+
+
+def run_torch_floor(args):
+    """E_c + E_c^H pairs per second of the plain-PyTorch FP32 operator and of
+    the library's FP32 operator in the same loop (same A_g, inputs resident,
+    CUDA events around 200 pairs after 20 warm-up pairs, L2 not flushed for
+    either)."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_05418_gb300 import gpjc, synth
+
+    dev = torch.device("cuda", 0)
+    wl = synth.workload(args.workload)
+    g = wl.geom
+    case = synth.make_case(wl)
+    plan = gpjc.Plan(g)
+    coils = torch.from_numpy(case.coils.astype(np.complex64)).to(dev)
+    roi = torch.from_numpy(case.roi).to(dev)
+    grp = gpjc.Groups.build(plan, coils, roi)
+    As, _ = grp.matrices()
+    op = gpjc.Operator(grp, coils, gpjc.FP32)
+    op.autotune()
+    tf = TorchFloor(g, case.coils, As, dev)
+    x = torch.from_numpy(case.rho.astype(np.complex64)).to(dev).reshape(g.shape)
+
+    def timed(pair, n=200, warm=20):
+        for _ in range(warm):
+            pair()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(n):
+            pair()
+        e1.record()
+        torch.cuda.synchronize()
+        return n / (e0.elapsed_time(e1) / 1e3)
+
+    a = tf.EH(tf.E(x))
+    b = op.EH(op.E(x))
+    torch.cuda.synchronize()
+    rel = float((a - b).abs().pow(2).sum().sqrt() / b.abs().pow(2).sum().sqrt())
+    v_torch = timed(lambda: tf.EH(tf.E(x)))
+    v_gpjc = timed(lambda: op.EH(op.E(x)))
+    out = {"impl": "torch-floor", "metric": "E_c+E_c^H pairs/s (single pairs, plain PyTorch FP32)",
+           "value": round(v_torch, 2), "unit": "pairs/s", "higher_is_better": True, "dtype": "f32",
+           "gpjc_fp32_same_loop": round(v_gpjc, 2), "gpjc_over_torch": round(v_gpjc / v_torch, 3),
+           "rel_l2_diff_EH_E": float(f"{rel:.3e}"),
+           "config": {"workload": wl.name, "matrix": [g.nz, g.ny, g.nx], "coils": g.nc, "os": g.os,
+                      "pairs": 200, "warmup_pairs": 20, "l2": "not flushed (both operators)"}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
@@ -552,6 +662,10 @@ def main():
         return
     if args.workload == "batch64":
         run_batch(args, rank, world, local)
+        return
+    if args.torch_floor:
+        if rank == 0:
+            run_torch_floor(args)
         return
     run_gpjc(args, rank, world, local)
 

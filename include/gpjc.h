@@ -181,7 +181,11 @@ gpjc_status gpjc_op_create(const gpjc_groups* groups, const float* d_coil, gpjc_
                            gpjc_op** out);
 void gpjc_op_destroy(gpjc_op* op);
 /* Times the readout-stage coil-chunk choices on `stream` and keeps the
- * fastest (synchronous); *nchunk receives it (may be NULL). */
+ * fastest (synchronous): the adjoint's chunk count, then the forward's, and
+ * for GPJC_BF16 / GPJC_FP16 operators the number of row pieces (1, 2, 4, 8)
+ * in which the adjoint's tensor-core expansion and inverse readout FFT run
+ * (the FP32 spectra of one piece stay in L2; the results do not depend on
+ * the split).  *nchunk receives the forward chunk count (may be NULL). */
 gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchunk);
 
 /* y = E_c x (Eq. 15): d_x [nz][ny][nx] -> d_y [n_lines][ntx_c]. */
