@@ -153,6 +153,26 @@ gpjc_status gpjc_groups_info_get(const gpjc_groups* groups, gpjc_groups_info* in
 /* h_A: as gpjc_groups_from_matrices.  h_ritz: [n_groups][block] Ritz values,
  * descending (NULL allowed).  Synchronous. */
 gpjc_status gpjc_groups_get(const gpjc_groups* groups, float* h_A, double* h_ritz);
+/* Kept dimension per group from the eigenvalue spectrum of P_g (Sec. 2.4,
+ * Eq. 8: the spectrum quantifies the compressibility and indicates N_s'):
+ * h_keep[g] = the smallest k >= 1 with
+ *   sum_{i<k} max(lambda_{g,i}, 0) >= threshold * trace_g,
+ * or -1 when the m given values do not reach it.
+ *   h_eig    [n_groups][m] leading eigenvalues of each group, descending
+ *            (e.g. the Ritz values of gpjc_groups_get, m = block), host
+ *   h_trace  [n_groups] trace(P_g), host, or NULL to use the sum of the m
+ *            given values (all N_s of them given).  trace(P_g) = |ROI| for
+ *            every group (gpjc_groups_info_get roi_pixels): each pixel's
+ *            normalised encoding vector (Eq. 11) contributes 1
+ *   threshold in (0, 1]
+ *   h_keep   [n_groups] int32 output, host
+ * Host only (no device work, no allocation).  GPJC_EINVAL for a null
+ * pointer, n_groups or m < 1, a threshold outside (0, 1] or a negative /
+ * non-finite trace; GPJC_ENONFINITE for a non-finite eigenvalue.  A new
+ * plan with these keeps takes the first h_keep[g] rows of each A_g
+ * (gpjc_groups_from_matrices): rows are in descending eigenvalue order. */
+gpjc_status gpjc_keep_from_energy(const double* h_eig, int32_t n_groups, int32_t m, const double* h_trace,
+                                  double threshold, int32_t* h_keep);
 /* h_P: [n_groups][N_s][N_s] complex128 Gram matrices (needs keep_gram). */
 gpjc_status gpjc_groups_gram(const gpjc_groups* groups, double* h_P);
 /* h_pix: [roi_pixels] raster indices of the ROI pixels used. */

@@ -253,6 +253,38 @@ def compression_matrix(P: np.ndarray, keep: int, nc: int, w: int, T=None):
     return A, ev
 
 
+def keep_from_energy(eigvals, threshold: float, trace=None) -> np.ndarray:
+    """Kept dimension per group from the eigenvalue spectrum of P_g (Eq. 8;
+    Sec. 2.4: the spectrum quantifies compressibility and indicates N_s').
+    Reading: N_s'_g is the smallest k >= 1 whose leading eigenvalues hold
+    at least `threshold` of the total, sum_{i<k} max(lambda_i, 0) >=
+    threshold * trace_g.  `eigvals` [G][m] holds the leading m eigenvalues
+    of each group, descending; trace_g defaults to their sum (all N_s of
+    them given) and otherwise is trace(P_g), which is |ROI| for every group
+    (each normalised pixel term of Eq. 11 has trace 1).  A group whose m
+    leading values do not reach the threshold gets -1."""
+    ev = np.asarray(eigvals, dtype=np.float64)
+    G = ev.shape[0]
+    if trace is None:  # summed in index order, as the running sum below
+        tr = []
+        for g in range(G):
+            t = 0.0
+            for k in range(ev.shape[1]):
+                t += max(float(ev[g, k]), 0.0)
+            tr.append(t)
+    else:
+        tr = list(np.broadcast_to(np.asarray(trace, dtype=np.float64), (G,)))
+    keep = np.full(G, -1, np.int64)
+    for g in range(G):
+        acc = 0.0
+        for k in range(ev.shape[1]):
+            acc += max(float(ev[g, k]), 0.0)
+            if acc >= threshold * tr[g]:
+                keep[g] = k + 1
+                break
+    return keep
+
+
 def build_groups(geom, coils, roi, T=None):
     """All groups: (A list, eigenvalue list, P list)."""
     roi_idx = roi_pixels(roi, coils)

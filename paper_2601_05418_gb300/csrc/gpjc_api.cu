@@ -648,6 +648,41 @@ extern "C" gpjc_status gpjc_groups_info_get(const gpjc_groups* gr, gpjc_groups_i
   return GPJC_OK;
 }
 
+// Kept dimension per group from the leading eigenvalues (Eq. 8; Sec. 2.4:
+// the spectrum of P_g indicates N_s'): the smallest k whose leading values
+// hold `threshold` of trace(P_g).  Host only.
+extern "C" gpjc_status gpjc_keep_from_energy(const double* h_eig, int32_t n_groups, int32_t m, const double* h_trace,
+                                             double threshold, int32_t* h_keep) {
+  if (!h_eig || !h_keep) return fail(GPJC_EINVAL, "null argument");
+  if (n_groups < 1 || m < 1) return fail(GPJC_EINVAL, "n_groups and m must be >= 1");
+  if (!(threshold > 0.0 && threshold <= 1.0)) return fail(GPJC_EINVAL, "threshold must be in (0, 1]");
+  for (int64_t i = 0; i < (int64_t)n_groups * m; ++i)
+    if (!std::isfinite(h_eig[i])) return fail(GPJC_ENONFINITE, "non-finite eigenvalue at %lld", (long long)i);
+  if (h_trace)
+    for (int g = 0; g < n_groups; ++g)
+      if (!std::isfinite(h_trace[g]) || h_trace[g] < 0.0) return fail(GPJC_EINVAL, "trace of group %d", g);
+  for (int g = 0; g < n_groups; ++g) {
+    const double* ev = h_eig + (size_t)g * m;
+    double tr = 0.0;
+    if (h_trace) {
+      tr = h_trace[g];
+    } else {
+      for (int k = 0; k < m; ++k) tr += std::max(ev[k], 0.0);  // index order
+    }
+    const double target = threshold * tr;
+    double acc = 0.0;
+    h_keep[g] = -1;
+    for (int k = 0; k < m; ++k) {
+      acc += std::max(ev[k], 0.0);
+      if (acc >= target) {
+        h_keep[g] = k + 1;
+        break;
+      }
+    }
+  }
+  return GPJC_OK;
+}
+
 extern "C" gpjc_status gpjc_groups_get(const gpjc_groups* gr, float* h_A, double* h_ritz) {
   if (!gr) return fail(GPJC_EINVAL, "null groups");
   const gpjc_plan* p = gr->plan;

@@ -84,6 +84,7 @@ _sig("gpjc_op_profile_read", [_P, C.c_int32, C.POINTER(C.c_double), _I32P])
 _sig("gpjc_groups_destroy", [_P], None)
 _sig("gpjc_groups_info_get", [_P, C.POINTER(GroupsInfo)])
 _sig("gpjc_groups_get", [_P, _P, _P])
+_sig("gpjc_keep_from_energy", [_P, C.c_int32, C.c_int32, _P, C.c_double, _P])
 _sig("gpjc_groups_gram", [_P, _P])
 _sig("gpjc_groups_roi", [_P, _I32P])
 _sig("gpjc_compress", [_P, _P, _P, C.c_int, _P])
@@ -121,6 +122,23 @@ def version() -> str:
 def launch_count() -> int:
     """Kernels launched by libgpjc so far in this process."""
     return int(_lib.gpjc_launch_count())
+
+
+def keep_from_energy(eigvals, threshold: float, trace=None) -> np.ndarray:
+    """Kept dimension per group: the smallest k whose leading eigenvalues of
+    P_g hold `threshold` of trace(P_g) (-1 if the given values do not reach
+    it).  eigvals [G][m] descending (e.g. Groups.matrices()[1]); trace: None
+    (sum of the given values), a scalar (|ROI|, the trace of every P_g) or
+    [G]."""
+    ev = np.ascontiguousarray(np.asarray(eigvals, dtype=np.float64))
+    G, m = ev.shape
+    tr = None
+    if trace is not None:
+        tr = np.ascontiguousarray(np.broadcast_to(np.asarray(trace, dtype=np.float64), (G,)))
+    keep = np.zeros(G, np.int32)
+    check(_lib.gpjc_keep_from_energy(ev.ctypes.data_as(_P), G, m, None if tr is None else tr.ctypes.data_as(_P),
+                                     float(threshold), keep.ctypes.data_as(_P)))
+    return keep
 
 
 STAGE_READOUT_FWD, STAGE_PHASE_ENCODE, STAGE_READOUT_ADJ = 0, 1, 2

@@ -88,3 +88,35 @@ def test_null_arguments(gpjc):
     assert lib.gpjc_recon(None, None, None, None, None, None) == gpjc.GPJC_EINVAL
     assert lib.gpjc_build_groups(None, None, None, None, None, None, C.byref(out)) == gpjc.GPJC_EINVAL
     assert b"null" in lib.gpjc_last_error()
+
+
+def test_keep_from_energy_matches_oracle(gpjc):
+    """The host-only keep policy of the C ABI takes the same integer decision
+    as the oracle (same FP64 running sums in index order) on random spectra
+    with ties, zeros and tiny negative values, with and without a trace."""
+    import oracle as O
+
+    rng = np.random.default_rng(11)
+    for trial in range(300):
+        G, m = int(rng.integers(1, 6)), int(rng.integers(1, 40))
+        ev = -np.sort(-np.round(rng.exponential(1.0, (G, m)), int(rng.integers(1, 4))), axis=1)
+        ev[:, -1] -= 1e-16 * rng.integers(0, 2, G)
+        tau = float(rng.choice([0.25, 0.5, 0.9, 0.99, 1.0, rng.uniform(0.01, 1.0)]))
+        trace = None if trial % 3 == 0 else float(np.sum(np.maximum(ev, 0), axis=1).max() * rng.uniform(1.0, 1.5))
+        got = gpjc.keep_from_energy(ev, tau, trace)
+        want = O.keep_from_energy(ev, tau, trace)
+        assert np.array_equal(got, want.astype(np.int32)), (trial, got, want)
+
+
+def test_keep_from_energy_rejects_bad_input(gpjc):
+    ev = np.array([[3.0, 2.0, 1.0]])
+    for tau in (0.0, -0.1, 1.5, float("nan")):
+        with pytest.raises(gpjc.GpjcError) as ei:
+            gpjc.keep_from_energy(ev, tau)
+        assert ei.value.status == gpjc.GPJC_EINVAL
+    with pytest.raises(gpjc.GpjcError) as ei:
+        gpjc.keep_from_energy(np.array([[3.0, float("inf")]]), 0.5)
+    assert ei.value.status == gpjc.GPJC_ENONFINITE
+    with pytest.raises(gpjc.GpjcError) as ei:
+        gpjc.keep_from_energy(ev, 0.5, trace=-1.0)
+    assert ei.value.status == gpjc.GPJC_EINVAL

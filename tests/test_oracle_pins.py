@@ -193,6 +193,63 @@ def test_compression_matrix_orthonormal_and_spectrum():
         assert np.abs(A @ P - ev[:A.shape[0], None] * A).max() < 1e-10
 
 
+def test_keep_from_energy_geometric_closed_form():
+    """lambda_i = r^i (i < n): the leading k hold (1 - r^k) / (1 - r^n) of the
+    total, so keep = ceil(log(1 - tau (1 - r^n)) / log r)."""
+    for r, n, tau in [(0.5, 20, 0.9), (0.8, 64, 0.99), (0.3, 10, 0.5), (0.95, 200, 0.999)]:
+        ev = r ** np.arange(n, dtype=np.float64)
+        k = math.ceil(math.log(1 - tau * (1 - r ** n)) / math.log(r))
+        assert O.keep_from_energy(ev[None], tau)[0] == k
+        # the same with the trace passed explicitly and the tail cut off
+        tr = (1 - r ** n) / (1 - r)
+        assert O.keep_from_energy(ev[None, :k + 1], tau, trace=tr)[0] == k
+        # fewer leading values than needed: -1
+        if k > 1:
+            assert O.keep_from_energy(ev[None, :k - 1], tau, trace=tr)[0] == -1
+
+
+def test_keep_from_energy_brute_force():
+    """Against a direct search over k on random spectra (ties, zeros and
+    tiny negative rounding values included)."""
+    rng = np.random.default_rng(7)
+    for _ in range(200):
+        m = int(rng.integers(1, 12))
+        ev = np.sort(np.round(rng.exponential(1.0, m), 1))[::-1]
+        ev[-1] -= 1e-15 * rng.integers(0, 2)
+        tau = float(rng.choice([0.3, 0.5, 0.9, 1.0]))
+        pos = np.maximum(ev, 0.0)
+        total = sum(float(v) for v in pos)
+        want = -1
+        for k in range(1, m + 1):
+            if sum(float(v) for v in pos[:k]) >= tau * total:
+                want = k
+                break
+        assert O.keep_from_energy(ev[None], tau)[0] == want
+
+
+def test_keep_from_energy_is_the_encoding_energy_kept():
+    """With trace(P_g) = |ROI| (one unit per normalised encoding vector,
+    Eq. 11), the energy left out by the first k eigenvectors is the squared
+    residual of the normalised encoding vectors outside their span (Eq. 8):
+    the chosen keep is the smallest k whose residual is at most
+    (1 - tau) |ROI|."""
+    g, c = _tiny2d(nx=8, ny=8, nc=3, os=2, cycles=2.0, n_groups=2)
+    roi = synth.roi_mask(synth.phantom(g.nx, g.ny))
+    idx = O.roi_pixels(roi, c)
+    for gi in range(g.n_groups):
+        P = O.gram(g, c, idx, gi)
+        _, ev = O.compression_matrix(P, g.nc * g.w, g.nc, g.w)
+        U = O.compression_matrix(P, g.nc * g.w, g.nc, g.w)[0].conj().T  # columns: eigenvectors, descending
+        V = O.encoding_vectors(g, c, idx, int(O.reference_patch(g.patch_group, g.n_groups)[gi]))
+        V = V / np.linalg.norm(V, axis=0, keepdims=True)
+        resid = [float(np.sum(np.abs(V - U[:, :k] @ (U[:, :k].conj().T @ V)) ** 2)) for k in range(len(ev) + 1)]
+        for tau in (0.5, 0.9, 0.99, 0.999):
+            k = O.keep_from_energy(ev[None], tau, trace=len(idx))[0]
+            assert 1 <= k <= len(ev)
+            assert resid[k] <= (1 - tau) * len(idx) + 1e-9 * len(idx)
+            assert resid[k - 1] > (1 - tau) * len(idx) - 1e-9 * len(idx)
+
+
 def test_keep_all_is_lossless():
     """keep = N_s: A_g unitary, ||E' x|| = ||E x||, CG on E' equals CG on E."""
     g, c = _tiny2d(nx=8, ny=6, nc=2, os=2, cycles=2.0, n_groups=2,
