@@ -312,6 +312,35 @@ def test_whitening():
 
 # ---------------------------------------------------------------- recon --
 
+def test_readout_rows_assemble_the_compressed_model():
+    """The per-row compressed readout matrices, followed by the sampled rows
+    of the centred phase-encode DFT, reproduce E_c (Eq. 14-15)."""
+    g, c = _tiny2d(nx=8, ny=12, nc=3, os=2, cycles=2.0, kappa_y=1.3, n_groups=2, keep=5,
+                   lines="regular", r=3)
+    As, _, _ = O.build_groups(g, c, np.ones(g.shape, np.uint8))
+    x = _rand(g.shape, 61)
+    H = np.stack([O.readout_Ec_row(g, c, As, y) @ x[0, y] for y in range(g.ny)])  # [y][N'_tx]
+    ky = np.asarray(g.line_ky)
+    F = np.exp(-2j * np.pi * np.outer(ky - g.ny // 2, O.centred(g.ny)) / g.ny) / math.sqrt(g.ny)
+    ref = O.Ec_apply(g, c, As, x)
+    assert np.linalg.norm(F @ H - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("r,keep", [(3, 8), (2, 6), (1, 3)])
+def test_decoupled_ls_is_the_global_least_squares(r, keep):
+    """Algorithm #1 (Sec. 3.4) on a regular mask with R | N_y returns the
+    least-squares solution of the whole compressed model (dense E' of
+    Eq. 14 solved by numpy's lstsq), noisy data included."""
+    g, c = _tiny2d(nx=8, ny=12, nc=3, os=2, cycles=2.0, kappa_y=1.3, n_groups=2, keep=keep,
+                   lines="regular", r=r)
+    As, _, _ = O.build_groups(g, c, np.ones(g.shape, np.uint8))
+    Sc = O.compress(g, As, O.E_apply(g, c, _rand(g.shape, 62))) + 0.05 * _rand((g.n_lines, O.ntx_compressed(g.patch_group, g.keep)), 63)
+    D = O.dense_Ec(g, c, As).reshape(-1, g.nx * g.ny)
+    x_ls = np.linalg.lstsq(D, Sc.ravel(), rcond=None)[0]
+    x_dec = O.decoupled_ls(g, c, As, Sc).ravel()
+    assert np.linalg.norm(x_dec - x_ls) < 1e-8 * np.linalg.norm(x_ls)
+
+
 def test_cg_reaches_least_squares():
     g, c = _tiny2d(nx=4, ny=4, nc=2, os=2, cycles=2.0, n_groups=2, keep=3)
     roi = np.ones(g.shape, np.uint8)
