@@ -225,6 +225,9 @@ def test_keep_from_energy_brute_force():
                 want = k
                 break
         assert O.keep_from_energy(ev[None], tau)[0] == want
+    # negative (rounding) eigenvalues add nothing to the total either: the
+    # default trace of [1, 0.5, -0.5] is 1.5, so the whole energy needs k = 2
+    assert O.keep_from_energy(np.array([[1.0, 0.5, -0.5]]), 1.0)[0] == 2
 
 
 def test_keep_from_energy_is_the_encoding_energy_kept():
