@@ -151,14 +151,15 @@ def peaks():
 DRAM_TRAFFIC = {("2d256", 2): 30536448}
 
 
-def k1_flops(g, ntxc, keep_avg):
+def k1_flops(g, ntxc, keep_avg, contraction=True):
     """Algorithmic FP32 flops of one readout-stage launch (all rows, all
     coils): coil multiply (6 N_x), pre-twiddle (6 N_tx), os FFTs of N_x
-    points (5 N_x log2 N_x each), wave/centring post-multiply (6 N_tx) and the
-    A_g contraction (8 flops per complex MAC, N_s'_g x w per patch and coil)."""
+    points (5 N_x log2 N_x each), wave/centring post-multiply (6 N_tx) and,
+    with `contraction`, the A_g contraction (8 flops per complex MAC,
+    N_s'_g x w per patch and coil)."""
     rows = g.ny * g.nz
     per_coil_row = (6 * g.nx + 6 * g.ntx + g.os * 5 * g.nx * math.log2(g.nx) + 6 * g.ntx
-                    + 8 * ntxc * g.w)
+                    + (8 * ntxc * g.w if contraction else 0))
     return rows * g.nc * per_coil_row
 
 
@@ -259,7 +260,9 @@ def run_gpjc(args, rank, world, local):
     dom = max(prof, key=lambda s: prof[s][0])
     dom_ms = prof[dom][0] / max(prof[dom][1], 1)
     keep_avg = float(np.mean(g.keep))
-    fl = k1_flops(g, plan.ntx_c, keep_avg)
+    # 16-bit operators: the A_g contraction runs on the tensor cores, so the
+    # FP32 ALU roofline of their readout stage counts the rest only
+    fl = k1_flops(g, plan.ntx_c, keep_avg, contraction=fp32)
     sm_mhz = clocks["sm_mhz"] or 2070.0
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled SM clock
     achieved = fl / (dom_ms * 1e-3) / 1e12
@@ -269,6 +272,10 @@ def run_gpjc(args, rank, world, local):
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled SM clock)",
                 "launch_ms": round(dom_ms, 5),
                 "stage_share": {names[s]: round(prof[s][0] / max(total_ms, 1e-9), 4) for s in prof}}
+    if not fp32:
+        roofline["alu_work"] = ("coil multiply, pre / post factors and readout FFTs; the A_g contraction "
+                                "(tensor_flop_per_launch) runs on the tensor cores")
+        roofline["tensor_flop_per_launch"] = k1_flops(g, plan.ntx_c, keep_avg) - fl
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
