@@ -244,7 +244,9 @@ __global__ void __launch_bounds__(kK1Threads) k1_sim_adj2(Geo g, const VT* __res
   }
 }
 
-
+// ------------------------------------------------------------------ host side --
+// (left out when the kernels above are compiled for a host emulation)
+#ifndef GPJC_DEVICE_SOURCE_ONLY
 constexpr size_t kSimSmemMax = 200 * 1024;
 
 // GPJC_SIM_LEGACY=1 keeps the one-coil kernels on two-pass lengths too (on the
@@ -339,5 +341,7 @@ cudaError_t launch_sim_adj_bf16(const Geo& g, const void* V, const float2* coil,
                                 cudaStream_t st) {
   return launch_sim_adj_t<__nv_bfloat162>(g, (const __nv_bfloat162*)V, coil, xpart, nchunk, 0, g.rows, st);
 }
+
+#endif  // GPJC_DEVICE_SOURCE_ONLY
 
 }  // namespace gpjc
