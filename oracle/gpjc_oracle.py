@@ -333,19 +333,20 @@ def EcH_apply(geom, coils, As, Sc) -> np.ndarray:
     return EH_apply(geom, coils, decompress_adjoint(geom, As, Sc))
 
 
-def readout_Ec_row(geom, coils, As, y: int) -> np.ndarray:
-    """Compressed readout encoding matrix of phase-encode row y (Eq. 14, 2D):
-    [N'_tx][N_x], entry (off_p + k, x) = sum_{n, tau} A_{g(p)}[k][n w + tau]
-    c_n(y, x) exp(-i [2 pi t_c x_c / N_tx + phi(t, y)]) / sqrt(N_tx),
-    t = p w + tau: the per-column matrix the paper stores (SI Table S2)."""
+def readout_Ec_row(geom, coils, As, y: int, z: int = 0) -> np.ndarray:
+    """Compressed readout encoding matrix of phase-encode row (y, z)
+    (Eq. 14): [N'_tx][N_x], entry (off_p + k, x) = sum_{n, tau}
+    A_{g(p)}[k][n w + tau] c_n(z, y, x) exp(-i [2 pi t_c x_c / N_tx +
+    phi(t, y, z)]) / sqrt(N_tx), t = p w + tau: the per-column matrix the
+    paper stores (SI Table S2)."""
     nx, nc, ntx, w = geom.nx, geom.nc, geom.ntx, geom.w
     xc = centred(nx)
     phi = wave_phase(geom)  # [t][z][y]
     Er = np.zeros((nc, ntx, nx), np.complex128)
     for n in range(nc):
         for t in range(ntx):
-            ph = 2 * PI * (t - ntx // 2) * xc / ntx + phi[t, 0, y]
-            Er[n, t] = coils[n, 0, y] * np.exp(-1j * ph) / math.sqrt(ntx)
+            ph = 2 * PI * (t - ntx // 2) * xc / ntx + phi[t, z, y]
+            Er[n, t] = coils[n, z, y] * np.exp(-1j * ph) / math.sqrt(ntx)
     off = patch_offsets(geom.patch_group, geom.keep)
     G = np.zeros((ntx_compressed(geom.patch_group, geom.keep), nx), np.complex128)
     for p, g in enumerate(geom.patch_group):
@@ -355,45 +356,69 @@ def readout_Ec_row(geom, coils, As, y: int) -> np.ndarray:
     return G
 
 
+def aliased_sets(geom):
+    """Phase-encode rows (raster z, y) grouped into the aliased sets of the
+    mask: the connected components of the nonzero pattern of
+    U = F^H M^T M F, F the centred unitary phase-encode DFT (Sec. 3.4:
+    regular / CAIPI masks give R-fold sets of discrete pixels).  Returns
+    (sets, F restricted to the sampled lines, U)."""
+    ny, nz = geom.ny, geom.nz
+    yc = np.tile(centred(ny), nz)
+    zc = np.repeat(centred(nz), ny)
+    kyc = np.asarray(geom.line_ky) - ny // 2
+    kzc = np.asarray(geom.line_kz) - nz // 2
+    F = np.exp(-2j * PI * (np.outer(kyc, yc) / ny + np.outer(kzc, zc) / nz)) / math.sqrt(ny * nz)
+    U = F.conj().T @ F
+    nz_pat = np.abs(U) > 1e-9 * np.abs(U).max()
+    parent = list(range(ny * nz))
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    for a, b in zip(*np.nonzero(nz_pat)):
+        ra, rb = find(int(a)), find(int(b))
+        if ra != rb:
+            parent[max(ra, rb)] = min(ra, rb)
+    sets = {}
+    for r in range(ny * nz):
+        sets.setdefault(find(r), []).append(r)
+    return [sets[k] for k in sorted(sets)], F, U
+
+
 def decoupled_ls(geom, coils, As, Sc) -> np.ndarray:
-    """Hybrid-space reconstruction (Sec. 3.4, algorithm #1) of the 2D least
-    squares problem of Eq. 16 for a regular phase-encode mask (every R-th
-    line, R dividing N_y), in the paper's three steps:
+    """Hybrid-space reconstruction (Sec. 3.4, algorithm #1) of the least
+    squares problem of Eq. 16, in the paper's three steps:
       1. inverse DFT of the zero-filled compressed k-space along the phase
-         encode: h~(y) = sum_ky F*[ky, y] S'(ky);
-      2. per aliased set Y = {y0 + j N_y / R}, the readout subproblem with
-         the R N_x pixels of Y as unknowns and h~ on Y as data: its normal
-         equations sum_{y''} G_y^H U[y, y''] G_y'' rho_y'' = G_y^H h~(y),
-         y, y'' in Y, with U = F^H M^T M F (nonzero only within a set) and
-         G_y the row's compressed readout matrix, solved by least squares
-         (minimum norm where singular);
+         encode: h~(y, z) = sum_lines F*[line, (y, z)] S'(line);
+      2. per aliased set Y (`aliased_sets`), the readout subproblem with the
+         |Y| N_x pixels of Y as unknowns and h~ on Y as data: its normal
+         equations sum_{r''} G_r^H U[r, r''] G_r'' rho_r'' = G_r^H h~(r),
+         r, r'' in Y, with G_r the row's compressed readout matrix, solved by
+         least squares (minimum norm where singular);
       3. assemble the rows of all sets into the image.
-    Exactly the global least-squares solution when the sets decouple."""
-    assert geom.nz == 1, "2D"
-    nx, ny = geom.nx, geom.ny
-    ky = np.asarray(geom.line_ky)
-    R = ny // len(ky)
-    assert R * len(ky) == ny and np.all(np.diff(ky) == R), "regular mask with R | N_y"
-    kyc = ky - ny // 2
-    yc = centred(ny)
-    F = np.exp(-2j * PI * np.outer(kyc, yc) / ny) / math.sqrt(ny)  # sampled rows of the centred DFT
-    ht = F.conj().T @ Sc  # step 1: [N_y][N'_tx]
-    U = F.conj().T @ F  # F^H M^T M F
-    Gs = [readout_Ec_row(geom, coils, As, y) for y in range(ny)]
-    rho = np.zeros((ny, nx), np.complex128)
-    step = ny // R
-    for y0 in range(step):  # step 2
-        Y = [y0 + j * step for j in range(R)]
-        N = np.zeros((R * nx, R * nx), np.complex128)
-        b = np.zeros(R * nx, np.complex128)
-        for a, ya in enumerate(Y):
-            b[a * nx:(a + 1) * nx] = Gs[ya].conj().T @ ht[ya]
-            for c, yb in enumerate(Y):
-                N[a * nx:(a + 1) * nx, c * nx:(c + 1) * nx] = Gs[ya].conj().T @ (U[ya, yb] * Gs[yb])
+    The sets decouple the normal equations exactly (U vanishes between
+    them), so this is the global least-squares solution; regular and CAIPI
+    masks give sets of R pixels."""
+    nx, ny, nz = geom.nx, geom.ny, geom.nz
+    sets, F, U = aliased_sets(geom)
+    ht = F.conj().T @ Sc  # step 1: [rows][N'_tx]
+    Gs = [readout_Ec_row(geom, coils, As, r % ny, r // ny) for r in range(ny * nz)]
+    rho = np.zeros((ny * nz, nx), np.complex128)
+    for Y in sets:  # step 2
+        m = len(Y)
+        N = np.zeros((m * nx, m * nx), np.complex128)
+        b = np.zeros(m * nx, np.complex128)
+        for a, ra in enumerate(Y):
+            b[a * nx:(a + 1) * nx] = Gs[ra].conj().T @ ht[ra]
+            for c, rb in enumerate(Y):
+                N[a * nx:(a + 1) * nx, c * nx:(c + 1) * nx] = Gs[ra].conj().T @ (U[ra, rb] * Gs[rb])
         sol = np.linalg.lstsq(N, b, rcond=None)[0]
-        for a, ya in enumerate(Y):  # step 3
-            rho[ya] = sol[a * nx:(a + 1) * nx]
-    return rho.reshape(1, ny, nx)
+        for a, ra in enumerate(Y):  # step 3
+            rho[ra] = sol[a * nx:(a + 1) * nx]
+    return rho.reshape(nz, ny, nx)
 
 
 def dense_Ec(geom, coils, As) -> np.ndarray:

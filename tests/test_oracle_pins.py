@@ -342,6 +342,24 @@ def test_decoupled_ls_is_the_global_least_squares(r, keep):
     x_ls = np.linalg.lstsq(D, Sc.ravel(), rcond=None)[0]
     x_dec = O.decoupled_ls(g, c, As, Sc).ravel()
     assert np.linalg.norm(x_dec - x_ls) < 1e-8 * np.linalg.norm(x_ls)
+    sets, _, _ = O.aliased_sets(g)
+    assert sorted(len(Y) for Y in sets) == [r] * (g.ny // r)
+
+
+def test_decoupled_ls_3d_caipi_is_the_global_least_squares():
+    """3x3 CAIPI on a 6 x 18 phase-encode grid (the shift pattern 0, 1, 2
+    closes within N_z, so the samples form a lattice): twelve aliased sets
+    of nine rows, and algorithm #1 equals the least-squares solution of the
+    dense 3D compressed model."""
+    g, c = _tiny3d(nx=6, ny=6, nz=18, nc=4, os=4, n_groups=2, lines="caipi", r=3)
+    As, _, _ = O.build_groups(g, c, np.ones(g.shape, np.uint8))
+    sets, _, _ = O.aliased_sets(g)
+    assert sorted(len(Y) for Y in sets) == [9] * 12
+    Sc = O.compress(g, As, O.E_apply(g, c, _rand(g.shape, 64))) + 0.05 * _rand((g.n_lines, O.ntx_compressed(g.patch_group, g.keep)), 65)
+    D = O.dense_Ec(g, c, As).reshape(-1, g.nx * g.ny * g.nz)
+    x_ls = np.linalg.lstsq(D, Sc.ravel(), rcond=None)[0]
+    x_dec = O.decoupled_ls(g, c, As, Sc).ravel()
+    assert np.linalg.norm(x_dec - x_ls) < 1e-8 * np.linalg.norm(x_ls)
 
 
 def test_cg_reaches_least_squares():
