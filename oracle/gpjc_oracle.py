@@ -546,19 +546,63 @@ def power_lipschitz(normal: Callable, v0: np.ndarray, iters: int) -> float:
     return L
 
 
+def tv_diff(u):
+    """Forward differences of a 2D image along x and y, zero across the last
+    column / row (Neumann boundary)."""
+    dx = np.zeros_like(u)
+    dy = np.zeros_like(u)
+    dx[:, :-1] = u[:, 1:] - u[:, :-1]
+    dy[:-1, :] = u[1:, :] - u[:-1, :]
+    return dx, dy
+
+
+def tv_diff_adj(px, py):
+    """Adjoint of `tv_diff`: (D_x^H p_x + D_y^H p_y)."""
+    out = np.zeros_like(px)
+    out[:, :-1] -= px[:, :-1]
+    out[:, 1:] += px[:, :-1]
+    out[:-1, :] -= py[:-1, :]
+    out[1:, :] += py[:-1, :]
+    return out
+
+
+def tv_smooth(u: np.ndarray, eps: float) -> float:
+    """Smoothed isotropic total variation of a 2D image (Eq. 17's TV term,
+    by a smooth approximation as Sec. 3.4 states):
+    sum_{y,x} sqrt(|D_x u|^2 + |D_y u|^2 + eps^2)."""
+    dx, dy = tv_diff(u)
+    return float(np.sum(np.sqrt(np.abs(dx) ** 2 + np.abs(dy) ** 2 + eps * eps)))
+
+
+def tv_smooth_grad(u: np.ndarray, eps: float) -> np.ndarray:
+    """Gradient of `tv_smooth` with respect to the real and imaginary parts,
+    as one complex image: D^H (D u / sqrt(|D u|^2 + eps^2)).  It is
+    Lipschitz with constant ||D||^2 / eps <= 8 / eps."""
+    dx, dy = tv_diff(u)
+    wgt = np.sqrt(np.abs(dx) ** 2 + np.abs(dy) ** 2 + eps * eps)
+    return tv_diff_adj(dx / wgt, dy / wgt)
+
+
 def fista(normal: Callable, b: np.ndarray, L: float, lam: float, levels: int,
-          iters: int, x0=None) -> np.ndarray:
+          iters: int, x0=None, lam_tv: float = 0.0, eps_tv: float = 1e-3) -> np.ndarray:
     """FISTA (Beck-Teboulle) for 1/2 ||E' x - S'||^2 + lam ||W x||_1 on the
-    detail bands (Eq. 17 with lambda_TV = 0):
-      x_k = W^H soft_{lam/L}(W (y_k - (E'^H E' y_k - E'^H S') / L)),
+    detail bands + lam_tv TV_eps(x) (Eq. 17, TV by its smooth approximation,
+    which joins the gradient step):
+      x_k = W^H soft_{lam/L}(W (y_k - (E'^H E' y_k - E'^H S'
+                                      + lam_tv grad TV_eps(y_k)) / L)),
       t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,
       y_{k+1} = x_k + ((t_k - 1) / t_{k+1}) (x_k - x_{k-1}).
-    Images are [nz][ny][nx]; the 2D transform runs per z-slice."""
+    L must bound the Lipschitz constant of the whole gradient (that of
+    E'^H E' plus 8 lam_tv / eps_tv).  Images are [nz][ny][nx]; the 2D
+    transforms run per z-slice."""
     x_prev = np.zeros_like(b) if x0 is None else x0.copy()
     y = x_prev.copy()
     t = 1.0
     for _ in range(iters):
-        z = y - (normal(y) - b) / L
+        grad = normal(y) - b
+        if lam_tv != 0.0:
+            grad = grad + lam_tv * np.stack([tv_smooth_grad(y[k], eps_tv) for k in range(y.shape[0])])
+        z = y - grad / L
         x = np.stack([wavelet_prox(z[k], lam / L, levels) for k in range(z.shape[0])])
         t_new = (1.0 + math.sqrt(1.0 + 4.0 * t * t)) / 2.0
         y = x + ((t - 1.0) / t_new) * (x - x_prev)

@@ -126,6 +126,27 @@ def lines_regular(ny: int, r: int):
     return ky, np.zeros_like(ky)
 
 
+def lines_variable_density(ny: int, accel: float, seed: int, center: int = 16, power: float = 2.0):
+    """Seeded 1D variable-density random phase-encode mask, a stand-in for
+    the Poisson-disc variable-density masks the paper draws with BART for
+    its compressed-sensing reconstructions: the `center` lines around
+    ky = N_y/2 always, the rest drawn without replacement with probability
+    proportional to (1 - |ky_c| / (N_y/2))^power until round(N_y / accel)
+    lines are taken.  Sorted, unique."""
+    n_take = max(1, int(round(ny / accel)))
+    kyc = np.arange(ny) - ny // 2
+    fixed = np.flatnonzero(np.abs(kyc + 0.5) < center / 2)
+    if len(fixed) >= n_take:
+        ky = np.sort(fixed[np.argsort(np.abs(kyc[fixed] + 0.5), kind="stable")[:n_take]])
+        return ky.astype(np.int32), np.zeros(len(ky), np.int32)
+    rest = np.setdiff1d(np.arange(ny), fixed)
+    wgt = np.maximum(1.0 - np.abs(kyc[rest]) / (ny / 2), 1e-6) ** power
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(rest, size=n_take - len(fixed), replace=False, p=wgt / wgt.sum())
+    ky = np.sort(np.concatenate([fixed, pick])).astype(np.int32)
+    return ky, np.zeros(len(ky), np.int32)
+
+
 def lines_caipi(ny: int, nz: int, ry: int, rz: int):
     """2D CAIPI: kz mod rz == 0 and ky mod ry == (kz / rz) mod ry.
     Sorted by (kz, ky)."""

@@ -427,6 +427,64 @@ def test_power_iteration_and_fista():
     assert np.abs(xf - xi).max() < 1e-6 * np.abs(xi).max()
 
 
+def test_tv_smooth_closed_forms_and_adjoint():
+    """Constant image: every term is eps.  Vertical edge (0 left, 1 right of
+    column c): the N_y terms at column c - 1 are sqrt(1 + eps^2), the rest
+    eps.  D^H is the adjoint of the forward differences."""
+    eps = 1e-2
+    ny, nx, c = 6, 9, 4
+    assert abs(O.tv_smooth(np.full((ny, nx), 2.5 + 1j), eps) - ny * nx * eps) < 1e-12
+    u = np.zeros((ny, nx), np.complex128)
+    u[:, c:] = 1.0
+    want = ny * math.sqrt(1 + eps * eps) + (ny * nx - ny) * eps
+    assert abs(O.tv_smooth(u, eps) - want) < 1e-12
+    v, px, py = _rand((ny, nx), 81), _rand((ny, nx), 82), _rand((ny, nx), 83)
+    dx, dy = O.tv_diff(v)
+    lhs = np.vdot(px, dx) + np.vdot(py, dy)
+    rhs = np.vdot(O.tv_diff_adj(px, py), v)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_tv_smooth_gradient_and_lipschitz():
+    """The gradient matches central differences of the function along random
+    complex directions, and never changes faster than 8 / eps."""
+    eps = 0.05
+    u = _rand((7, 8), 84)
+    gr = O.tv_smooth_grad(u, eps)
+    for seed in range(5):
+        d = _rand((7, 8), 90 + seed)
+        h = 1e-6
+        fd = (O.tv_smooth(u + h * d, eps) - O.tv_smooth(u - h * d, eps)) / (2 * h)
+        assert abs(fd - np.vdot(gr, d).real) < 1e-6 * max(1.0, abs(fd))
+    rng = np.random.default_rng(85)
+    for _ in range(50):
+        a = _rand((7, 8), int(rng.integers(1 << 30)))
+        b = a + 0.01 * _rand((7, 8), int(rng.integers(1 << 30)))
+        ratio = np.linalg.norm(O.tv_smooth_grad(a, eps) - O.tv_smooth_grad(b, eps)) / np.linalg.norm(a - b)
+        assert ratio <= 8 / eps * (1 + 1e-9)
+
+
+def test_fista_with_tv_reaches_its_optimality_condition():
+    """Wavelet weight 0, TV weight > 0: the objective is smooth and strongly
+    convex here (full-rank E'), and FISTA's limit zeroes its gradient
+    E'^H (E' x - S') + lam_tv grad TV_eps(x); with lam_tv = 0 it is the
+    plain FISTA iteration."""
+    g, c = _tiny2d(nx=8, ny=8, nc=2, os=2, cycles=2.0, n_groups=2, keep=4, lines="regular", r=2)
+    As, _, _ = O.build_groups(g, c, np.ones(g.shape, np.uint8))
+    pb = O.Problem(g, c, As)
+    Sc = pb.Ec(_rand(g.shape, 86))
+    b = pb.EcH(Sc)
+    L0 = O.power_lipschitz(pb.normal_c, _rand(g.shape, 87), 500)
+    assert np.array_equal(O.fista(pb.normal_c, b, L0, 0.01, 2, 30),
+                          O.fista(pb.normal_c, b, L0, 0.01, 2, 30, lam_tv=0.0))
+    lam_tv, eps = 0.02, 0.1
+    L = 1.01 * L0 + 8 * lam_tv / eps
+    x = O.fista(pb.normal_c, b, L, 0.0, 2, 4000, lam_tv=lam_tv, eps_tv=eps)
+    grad = pb.normal_c(x) - b + lam_tv * O.tv_smooth_grad(x[0], eps)[None]
+    assert np.linalg.norm(grad) < 1e-7 * np.linalg.norm(b)
+    assert np.linalg.norm(lam_tv * O.tv_smooth_grad(x[0], eps)) > 1e-3 * np.linalg.norm(b)  # the TV term acts
+
+
 def test_nrmse_closed_form():
     ref = np.zeros((1, 4, 4), complex)
     ref[0, 0, 0] = 2.0
@@ -487,3 +545,18 @@ def test_roi_pixels_raster_and_coverage():
     c = np.ones((2, 1, 3, 4), complex)
     c[:, 0, 2, 0] = 0  # a pixel no coil sees
     assert list(O.roi_pixels(roi, c)) == [3, 6]
+
+
+def test_variable_density_lines():
+    """Seeded variable-density mask: reproducible, sorted and unique, the
+    requested count, the centre always sampled, denser near the centre."""
+    ny, accel = 256, 4
+    a = synth.lines_variable_density(ny, accel, 5)
+    b = synth.lines_variable_density(ny, accel, 5)
+    assert np.array_equal(a[0], b[0]) and np.all(a[1] == 0)
+    ky = a[0]
+    assert len(ky) == 64 and np.all(np.diff(ky) > 0) and ky.min() >= 0 and ky.max() < ny
+    assert set(range(ny // 2 - 8, ny // 2 + 8)) <= set(ky.tolist())
+    kyc = np.abs(ky - ny // 2)
+    assert np.sum(kyc < ny // 8) > np.sum(kyc >= 3 * ny // 8)
+    assert not np.array_equal(ky, synth.lines_variable_density(ny, accel, 6)[0])
