@@ -626,6 +626,100 @@ def nrmse_mag(x: np.ndarray, ref: np.ndarray) -> float:
 
 # ============================================================ pipeline ==
 
+# ============================================== nonlinear B0 modulation ==
+# Local B0 coils (Sec. 2.1-2.2, Eq. 2-3): the modulation phase depends on the
+# readout position as well, phi(t, r) = sum_lambda a_lambda(t) B_lambda(r),
+# so the readout is no longer a DFT and the compressed readout encoding of
+# each phase-encode row is a stored matrix (Eq. 14).  The phase-encode DFT
+# still factors out because phi does not depend on the phase-encode step.
+
+def local_b0_phase(fields: np.ndarray, amps: np.ndarray) -> np.ndarray:
+    """phi[t][z][y][x] = sum_lambda amps[lambda][t] fields[lambda][z][y][x]
+    (radians): the time-varying fields of the local B0 coils (Eq. 2-3)."""
+    return np.einsum("lt,lzyx->tzyx", np.asarray(amps, np.float64), np.asarray(fields, np.float64))
+
+
+def dense_E_phase(geom, coils: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    """Brute-force encoding matrix (Eq. 1, 4) for a general modulation phase
+    phi[t][z][y][x]: rows (line, coil, t), columns raster (z, y, x)."""
+    nx, ny, nz, nc, ntx = geom.nx, geom.ny, geom.nz, geom.nc, geom.ntx
+    L = nx * ny * nz
+    zc, yc, xc = np.meshgrid(centred(nz), centred(ny), centred(nx), indexing="ij")
+    zc, yc, xc = zc.ravel(), yc.ravel(), xc.ravel()
+    ph_r = phi.reshape(ntx, L)
+    tc = centred(ntx)
+    E = np.zeros((geom.n_lines * nc * ntx, L), np.complex128)
+    norm = 1.0 / math.sqrt(ntx * ny * nz)
+    cmap = coils.reshape(nc, L)
+    row = 0
+    for ky, kz in zip(geom.line_ky, geom.line_kz):
+        kyc, kzc = ky - ny // 2, kz - nz // 2
+        for n in range(nc):
+            for t in range(ntx):
+                ph = (2 * PI * tc[t] * xc / ntx + 2 * PI * kyc * yc / ny
+                      + 2 * PI * kzc * zc / nz + ph_r[t])
+                E[row] = cmap[n] * np.exp(-1j * ph) * norm
+                row += 1
+    return E
+
+
+def readout_row_phase(geom, coils, As, phi: np.ndarray, y: int, z: int = 0) -> np.ndarray:
+    """Compressed readout encoding matrix E'_g of phase-encode row (y, z) for
+    a general phase (Eq. 14): [N'_tx][N_x], entry (off_p + k, x) =
+    sum_{n,tau} A_{g(p)}[k][n w + tau] c_n(z,y,x)
+    exp(-i [2 pi t_c x_c / N_tx + phi(t,z,y,x)]) / sqrt(N_tx), t = p w + tau."""
+    nx, nc, ntx, w = geom.nx, geom.nc, geom.ntx, geom.w
+    xc = centred(nx)
+    Er = np.zeros((nc, ntx, nx), np.complex128)
+    for n in range(nc):
+        for t in range(ntx):
+            ph = 2 * PI * (t - ntx // 2) * xc / ntx + phi[t, z, y, :]
+            Er[n, t] = coils[n, z, y] * np.exp(-1j * ph) / math.sqrt(ntx)
+    off = patch_offsets(geom.patch_group, geom.keep)
+    G = np.zeros((ntx_compressed(geom.patch_group, geom.keep), nx), np.complex128)
+    for p, g in enumerate(geom.patch_group):
+        k = int(geom.keep[g])
+        G[off[p]:off[p] + k] = As[g] @ Er[:, p * w:(p + 1) * w, :].reshape(nc * w, nx)
+    return G
+
+
+def Ec_apply_phase(geom, coils, As, phi: np.ndarray, rho: np.ndarray) -> np.ndarray:
+    """E' rho for a general phase: every row's stored readout matrix, then
+    the centred unitary phase-encode DFT and the line gather (Eq. 14-15)."""
+    nx, ny, nz = geom.nx, geom.ny, geom.nz
+    H = np.stack([readout_row_phase(geom, coils, As, phi, r % ny, r // ny) @ rho[r // ny, r % ny]
+                  for r in range(ny * nz)])  # [rows][N'_tx]
+    yc = np.tile(centred(ny), nz)
+    zc = np.repeat(centred(nz), ny)
+    kyc = np.asarray(geom.line_ky) - ny // 2
+    kzc = np.asarray(geom.line_kz) - nz // 2
+    F = np.exp(-2j * PI * (np.outer(kyc, yc) / ny + np.outer(kzc, zc) / nz)) / math.sqrt(ny * nz)
+    return F @ H
+
+
+def gram_phase(geom, coils, roi_idx, g: int, phi: np.ndarray, T=None) -> np.ndarray:
+    """P_g (Eq. 7-11) for a general phase: encoding vectors of the group's
+    first patch, entry (n, tau) = c~_n(r) exp(-i [2 pi t_c x_c / N_tx +
+    phi(t, r)]), normalised per pixel."""
+    nx, ny, nc, w = geom.nx, geom.ny, geom.nc, geom.w
+    L = nx * ny * geom.nz
+    c = coils.reshape(nc, L)
+    if T is not None:
+        c = T @ c
+    c = c[:, roi_idx]
+    xc = roi_idx % nx - nx // 2
+    ph_r = phi.reshape(geom.ntx, L)[:, roi_idx]
+    patch = int(reference_patch(geom.patch_group, geom.n_groups)[g])
+    Eg = np.empty((nc * w, len(roi_idx)), np.complex128)
+    for tau in range(w):
+        t = patch * w + tau
+        e = np.exp(-1j * (2 * PI * (t - geom.ntx // 2) * xc / geom.ntx + ph_r[t]))
+        for n in range(nc):
+            Eg[n * w + tau] = c[n] * e
+    Nd = 1.0 / np.sum(np.abs(Eg) ** 2, axis=0)
+    return (Eg * Nd[None, :]) @ Eg.conj().T
+
+
 class Problem:
     """Convenience bundle: operators bound to one geometry and coil set."""
 

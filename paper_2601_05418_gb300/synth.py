@@ -147,6 +147,31 @@ def lines_variable_density(ny: int, accel: float, seed: int, center: int = 16, p
     return ky, np.zeros(len(ky), np.int32)
 
 
+def local_b0_fields(nx: int, ny: int, nz: int, n_fields: int, seed: int, peak: float = 6.0) -> np.ndarray:
+    """Seeded synthetic fields of local B0 coils (no measured field maps
+    exist here): smooth Gaussian bumps [n_fields][nz][ny][nx] centred near
+    the edge of the field of view, width 0.3 FOV, in radians at unit
+    amplitude (peak radians at the bump centre)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    zz, yy, xx = np.meshgrid((np.arange(nz) - nz / 2) / max(nz, 1), (np.arange(ny) - ny / 2) / ny,
+                             (np.arange(nx) - nx / 2) / nx, indexing="ij")
+    out = np.zeros((n_fields, nz, ny, nx))
+    for k in range(n_fields):
+        ang = 2 * np.pi * (k + rng.uniform(-0.2, 0.2)) / n_fields
+        cy, cx = 0.45 * np.sin(ang), 0.45 * np.cos(ang)
+        out[k] = peak * np.exp(-((yy - cy) ** 2 + (xx - cx) ** 2 + zz ** 2) / (2 * 0.3 ** 2))
+    return out
+
+
+def local_b0_amplitudes(ntx: int, cycles: float, n_fields: int, seed: int) -> np.ndarray:
+    """Seeded sinusoidal drive of each local B0 coil over the readout,
+    a_k(t) = sin(2 pi cycles t / N_tx + phase_k), [n_fields][ntx]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = np.arange(ntx)
+    ph = rng.uniform(0, 2 * np.pi, n_fields)
+    return np.sin(2 * np.pi * cycles * t[None, :] / ntx + ph[:, None])
+
+
 def lines_caipi(ny: int, nz: int, ry: int, rz: int):
     """2D CAIPI: kz mod rz == 0 and ky mod ry == (kz / rz) mod ry.
     Sorted by (kz, ky)."""

@@ -560,3 +560,47 @@ def test_variable_density_lines():
     kyc = np.abs(ky - ny // 2)
     assert np.sum(kyc < ny // 8) > np.sum(kyc >= 3 * ny // 8)
     assert not np.array_equal(ky, synth.lines_variable_density(ny, accel, 6)[0])
+
+
+def _wave_as_field(g):
+    """The linear wave of Eq. 3 written as one local field 2 pi y_c / N_y
+    driven by a_y(t): the general-phase functions must reduce to the wave
+    ones."""
+    ay, _ = O.wave_coeffs(g.ntx, g.cycles, g.kappa_y, g.kappa_z)
+    field = np.broadcast_to((2 * np.pi * O.centred(g.ny) / g.ny)[None, None, :, None],
+                            (1, g.nz, g.ny, g.nx)).copy()
+    return O.local_b0_phase(field, ay[None, :])
+
+
+def test_general_phase_reduces_to_the_wave():
+    g, c = _tiny2d(nx=8, ny=6, nc=3, os=2, cycles=2.0, kappa_y=1.3, n_groups=2, keep=4, lines="regular", r=2)
+    phi = _wave_as_field(g)
+    assert np.abs(phi[:, :, :, 3] - O.wave_phase(g)).max() < 1e-12
+    roi = synth.roi_mask(synth.phantom(g.nx, g.ny))
+    As, _, Ps = O.build_groups(g, c, roi)
+    idx = O.roi_pixels(roi, c)
+    for gi in range(g.n_groups):
+        assert np.abs(O.gram_phase(g, c, idx, gi, phi) - Ps[gi]).max() < 1e-11 * len(idx)
+    x = _rand(g.shape, 101)
+    ref = O.Ec_apply(g, c, As, x)
+    assert np.linalg.norm(O.Ec_apply_phase(g, c, As, phi, x) - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+def test_nonlinear_local_b0_model_equals_dense_E():
+    """Three synthetic local B0 coils (x-dependent phase): the stored
+    per-row readout matrices with the phase-encode DFT equal the compressed
+    brute-force E (Eq. 1, 4, 13-14); the Gram keeps trace |ROI|."""
+    g, c = _tiny2d(nx=8, ny=6, nc=3, os=2, cycles=2.0, kappa_y=0.0, n_groups=2, keep=4, lines="regular", r=2)
+    phi = O.local_b0_phase(synth.local_b0_fields(g.nx, g.ny, 1, 3, 102), synth.local_b0_amplitudes(g.ntx, 2.0, 3, 103))
+    assert np.ptp(phi[:, 0, 2, :], axis=1).max() > 0.5  # the phase varies along the readout
+    roi = synth.roi_mask(synth.phantom(g.nx, g.ny))
+    idx = O.roi_pixels(roi, c)
+    Ps = [O.gram_phase(g, c, idx, gi, phi) for gi in range(g.n_groups)]
+    As = [O.compression_matrix(P, int(g.keep[gi]), g.nc, g.w)[0] for gi, P in enumerate(Ps)]
+    for P in Ps:
+        assert abs(np.trace(P).real - len(idx)) < 1e-12 * len(idx)
+        assert np.linalg.eigvalsh(P).min() > -1e-12 * len(idx)
+    x = _rand(g.shape, 104)
+    S = (O.dense_E_phase(g, c, phi) @ x.ravel()).reshape(g.n_lines, g.nc, g.ntx)
+    ref = O.compress(g, As, S)
+    assert np.linalg.norm(O.Ec_apply_phase(g, c, As, phi, x) - ref) < 1e-12 * np.linalg.norm(ref)
