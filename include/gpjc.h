@@ -153,6 +153,20 @@ gpjc_status gpjc_groups_info_get(const gpjc_groups* groups, gpjc_groups_info* in
 /* h_A: as gpjc_groups_from_matrices.  h_ritz: [n_groups][block] Ritz values,
  * descending (NULL allowed).  Synchronous. */
 gpjc_status gpjc_groups_get(const gpjc_groups* groups, float* h_A, double* h_ritz);
+/* Gradient of the smoothed isotropic total variation, the TV term of the
+ * regularised reconstruction (Eq. 17; Sec. 3.4 uses a smooth approximation):
+ *   TV_eps(x) = sum_{y,x} sqrt(|D_x x|^2 + |D_y x|^2 + eps^2) per z-slice,
+ *   d_g = D^H (D x / sqrt(|D x|^2 + eps^2)),
+ * forward differences, no difference across the last column / row.
+ *   d_x, d_g  [nz][ny][nx] complex64, device, caller-owned; d_g must not
+ *             alias d_x
+ *   eps       > 0
+ * Asynchronous on `stream`; allocates nothing.  GPJC_EINVAL for null or
+ * aliased pointers, a dimension < 1 or eps <= 0; GPJC_ECUDA if the launch
+ * fails. */
+gpjc_status gpjc_tv_grad(const float* d_x, int32_t nz, int32_t ny, int32_t nx, double eps, float* d_g,
+                         void* stream);
+
 /* Kept dimension per group from the eigenvalue spectrum of P_g (Sec. 2.4,
  * Eq. 8: the spectrum quantifies the compressibility and indicates N_s'):
  * h_keep[g] = the smallest k >= 1 with

@@ -648,6 +648,18 @@ extern "C" gpjc_status gpjc_groups_info_get(const gpjc_groups* gr, gpjc_groups_i
   return GPJC_OK;
 }
 
+// Gradient of the smoothed TV of Eq. 17 (Sec. 3.4: TV by a smooth
+// approximation), per z-slice.  Asynchronous on `stream`.
+extern "C" gpjc_status gpjc_tv_grad(const float* d_x, int32_t nz, int32_t ny, int32_t nx, double eps, float* d_g,
+                                    void* stream) {
+  if (!d_x || !d_g) return fail(GPJC_EINVAL, "null argument");
+  if (nz < 1 || ny < 1 || nx < 1) return fail(GPJC_EINVAL, "image dimensions must be >= 1");
+  if (!(eps > 0.0) || !std::isfinite(eps)) return fail(GPJC_EINVAL, "eps must be finite and > 0");
+  if ((const void*)d_x == (const void*)d_g) return fail(GPJC_EINVAL, "d_g must not alias d_x");
+  CK(launch_tv_grad((const float2*)d_x, (float2*)d_g, nz, ny, nx, (float)eps, (cudaStream_t)stream));
+  return GPJC_OK;
+}
+
 // Kept dimension per group from the leading eigenvalues (Eq. 8; Sec. 2.4:
 // the spectrum of P_g indicates N_s'): the smallest k whose leading values
 // hold `threshold` of trace(P_g).  Host only.

@@ -26,6 +26,8 @@ cudaError_t launch_sim_fwd_bf16(const Geo& g, const float2* x, const float2* coi
                                 cudaStream_t st);
 cudaError_t launch_sim_adj(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
                            cudaStream_t st);
+// gradient of the smoothed isotropic TV of each z-slice (k_tv.cu)
+cudaError_t launch_tv_grad(const float2* u, float2* g, int nz, int ny, int nx, float eps, cudaStream_t st);
 // rows [row0, row0 + nrows) only (the other rows' partial images are untouched)
 cudaError_t launch_sim_adj_rows(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
                                 int row0, int nrows, cudaStream_t st);

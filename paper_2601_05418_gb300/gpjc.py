@@ -85,6 +85,7 @@ _sig("gpjc_groups_destroy", [_P], None)
 _sig("gpjc_groups_info_get", [_P, C.POINTER(GroupsInfo)])
 _sig("gpjc_groups_get", [_P, _P, _P])
 _sig("gpjc_keep_from_energy", [_P, C.c_int32, C.c_int32, _P, C.c_double, _P])
+_sig("gpjc_tv_grad", [_P, C.c_int32, C.c_int32, C.c_int32, C.c_double, _P, _P])
 _sig("gpjc_groups_gram", [_P, _P])
 _sig("gpjc_groups_roi", [_P, _I32P])
 _sig("gpjc_compress", [_P, _P, _P, C.c_int, _P])
@@ -122,6 +123,17 @@ def version() -> str:
 def launch_count() -> int:
     """Kernels launched by libgpjc so far in this process."""
     return int(_lib.gpjc_launch_count())
+
+
+def tv_grad(x: torch.Tensor, eps: float, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Gradient of the smoothed isotropic TV of each z-slice of a
+    [nz][ny][nx] complex64 image on the device."""
+    nz, ny, nx = x.shape
+    if out is None:
+        out = torch.empty_like(x)
+    check(_lib.gpjc_tv_grad(_dptr(x, torch.complex64), nz, ny, nx, float(eps), _dptr(out, torch.complex64),
+                            _stream(stream)))
+    return out
 
 
 def keep_from_energy(eigvals, threshold: float, trace=None) -> np.ndarray:

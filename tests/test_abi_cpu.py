@@ -120,3 +120,14 @@ def test_keep_from_energy_rejects_bad_input(gpjc):
     with pytest.raises(gpjc.GpjcError) as ei:
         gpjc.keep_from_energy(ev, 0.5, trace=-1.0)
     assert ei.value.status == gpjc.GPJC_EINVAL
+
+
+def test_tv_grad_rejects_bad_input_before_launch(gpjc):
+    lib = gpjc.lib()
+    buf = C.c_void_p(16)  # never dereferenced: every call below fails validation first
+    assert lib.gpjc_tv_grad(None, 1, 4, 4, 0.1, buf, None) == gpjc.GPJC_EINVAL
+    assert lib.gpjc_tv_grad(buf, 1, 4, 4, 0.1, None, None) == gpjc.GPJC_EINVAL
+    assert lib.gpjc_tv_grad(buf, 0, 4, 4, 0.1, C.c_void_p(32), None) == gpjc.GPJC_EINVAL
+    assert lib.gpjc_tv_grad(buf, 1, 4, 4, 0.0, C.c_void_p(32), None) == gpjc.GPJC_EINVAL
+    assert lib.gpjc_tv_grad(buf, 1, 4, 4, float("nan"), C.c_void_p(32), None) == gpjc.GPJC_EINVAL
+    assert lib.gpjc_tv_grad(buf, 1, 4, 4, 0.1, buf, None) == gpjc.GPJC_EINVAL
