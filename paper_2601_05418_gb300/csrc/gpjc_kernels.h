@@ -40,7 +40,7 @@ cudaError_t launch_pe_normal(const Geo& g, const float2* Hpart, int nchunk, int 
                              double* partials, unsigned* counter, double* qq, cudaStream_t st);
 int pe_normal_blocks(const Geo& g, int ncols);
 
-// ---- register-tiled readout stage (k_readout.cu)
+// ---- register-tiled readout stage (k_readout_f.cu, k_readout_a.cu, k_readout_a2.cu)
 struct ReadoutGeomHost {
   int G, w, ntx, ntxc;
   std::vector<int> pg, keep, poff, aoff;
@@ -54,8 +54,10 @@ cudaError_t launch_k1f_tiled(const Geo& g, const RTiles& tl, const float2* x, co
                              const float2* AT, float2* Hpart, int nchunk, cudaStream_t st);
 cudaError_t launch_k1a_tiled(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,
                              const float2* A, float2* xpart, int nchunk, cudaStream_t st);
+cudaError_t launch_k1a_tiled_ts2(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,
+                                 const float2* A, float2* xpart, int nchunk, cudaStream_t st);
 
-// ---- batched persistent CG (k_readout.cu)
+// ---- batched persistent CG (k_batch.cu)
 size_t batch_pe_smem(const Geo& g);
 cudaError_t launch_batch_cg(const BatchPlan& bp, int grid, size_t smem, cudaStream_t st);
 int batch_max_blocks(size_t smem);

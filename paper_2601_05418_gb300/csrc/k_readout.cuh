@@ -1,3 +1,7 @@
+// Device bodies of the FP32 register-tiled readout stage, shared by the
+// single-slice kernels (k_readout_f.cu, k_readout_a.cu, k_readout_a2.cu)
+// and the persistent batch kernel (k_batch.cu).
+//
 // Readout stage of E_c and E_c^H, FP32, register-tiled (Eq. 13-15).
 //
 // A block owns RB phase-encode rows and a chunk of coils.  Per coil, each
@@ -14,6 +18,7 @@
 // The tiles (group, first kept component / first sample, up to 4 columns)
 // are listed on the host per geometry and RB (plan tables), so any patch ->
 // group map and any per-group keep are handled by the same kernels.
+#pragma once
 #include "gpjc_device.cuh"
 #include "gpjc_kernels.h"
 
@@ -31,20 +36,11 @@ __host__ __device__ inline int u_stride(int ntx) { return (ntx + 7) & ~7; }
 __host__ __device__ inline int upad(int i) { return i + 2 * (i >> 3); }
 __host__ __device__ inline int upad_size(int n) { return n + 2 * (n >> 3) + 2; }
 
-size_t readout_fwd_smem(const Geo& g, int rb) {
-  const int st = u_stride(g.ntx);
-  return sizeof(float2) * (size_t)(upad_size(rb * st) + 2 * spad_size(g.ntx) + g.nx);
-}
 // staged H2 rows: one padding slot every 16 columns (conflict-free when the
 // tiles of a warp read columns 16 kept components apart)
 __host__ __device__ inline int hpad(int i) { return i + (i >> 4); }
 __host__ __device__ inline int hpad_size(int n) { return n + (n >> 4) + 1; }
 
-size_t readout_adj_smem(const Geo& g, int rb, int hstage) {
-  const int st = u_stride(g.ntx);
-  return sizeof(float2) *
-         (size_t)(spad_size(rb * st) + spad_size(g.ntx) + g.nx + (hstage ? hpad_size(rb * g.ntxc) : 0));
-}
 
 __device__ __forceinline__ float2 post_at(const Geo& g, int t, int row) {
   const int y = row % g.ny, z = row / g.ny;
@@ -389,332 +385,6 @@ __global__ void __launch_bounds__(kRThreads) k1a_tiled(Geo g, RTiles tl, const f
                                                        int cpc) {
   extern __shared__ float2 rsm[];
   k1a_body<MAXX, false, TS>(g, tl, H2, coil, Arow, xpart, cpc, blockIdx.x, blockIdx.y, rsm);
-}
-
-}  // namespace gpjc
-
-namespace gpjc {
-
-// ------------------------------------------------------------------ host side --
-static int ceil_div(int a, int b) { return (a + b - 1) / b; }
-
-void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, int ts, std::vector<int4>* hdr,
-                         std::vector<int4>* cols) {
-  const int st = u_stride(h.ntx);
-  std::vector<std::vector<int>> occ(h.G);
-  for (int p = 0; p < (int)h.pg.size(); ++p) occ[h.pg[p]].push_back(p);
-  hdr->clear();
-  cols->clear();
-  for (int g = 0; g < h.G; ++g) {
-    const int oc = (int)occ[g].size();
-    const int ncol = rb * oc;
-    const int inner = adjoint ? h.w : h.keep[g];  // samples (adjoint) or kept components (forward)
-    const int step = adjoint ? ts : 4;
-    for (int i0 = 0; i0 < inner; i0 += step) {
-      for (int c0 = 0; c0 < ncol; c0 += 4) {
-        hdr->push_back(make_int4(h.aoff[g] + i0, h.keep[g], std::min(step, inner - i0), 0));
-        for (int c = 0; c < 4; ++c) {
-          const int cc = c0 + c;
-          if (cc >= ncol) {
-            cols->push_back(make_int4(-1, -1, 0, 0));
-            continue;
-          }
-          const int r = cc / oc, p = occ[g][cc % oc];
-          if (adjoint)
-            cols->push_back(make_int4(r, h.poff[p], p * h.w + i0, 0));
-          else
-            cols->push_back(make_int4(r * st + p * h.w, r * h.ntxc + h.poff[p] + i0, 0, 0));
-        }
-      }
-    }
-  }
-}
-
-int readout_tile_count(const ReadoutGeomHost& h, int rb, bool adjoint, int ts) {
-  std::vector<std::vector<int>> occ(h.G);
-  for (int p = 0; p < (int)h.pg.size(); ++p) occ[h.pg[p]].push_back(p);
-  int n = 0;
-  for (int g = 0; g < h.G; ++g)
-    n += ceil_div(adjoint ? h.w : h.keep[g], adjoint ? ts : 4) * ceil_div(rb * (int)occ[g].size(), 4);
-  return n;
-}
-
-template <int MAXT>
-static cudaError_t launch_f(const Geo& g, const RTiles& tl, const float2* x, const float2* coil, const float2* AT,
-                            float2* Hpart, int nchunk, cudaStream_t st) {
-  const int cpc = (g.nc + nchunk - 1) / nchunk;
-  const size_t sm = readout_fwd_smem(g, tl.rb);
-  static int attr = 0;
-  if ((int)sm > attr) {
-    cudaFuncSetAttribute(k1f_tiled<MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k1f_tiled<MAXT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    attr = (int)sm;
-  }
-  dim3 grid((g.rows + tl.rb - 1) / tl.rb, nchunk);
-  note_launches(1); k1f_tiled<MAXT><<<grid, kRThreads, sm, st>>>(g, tl, x, coil, AT, Hpart, cpc);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_k1f_tiled(const Geo& g, const RTiles& tl, const float2* x, const float2* coil,
-                             const float2* AT, float2* Hpart, int nchunk, cudaStream_t st) {
-  const int maxt = ceil_div(tl.nt, kRThreads);
-  if (maxt <= 1) return launch_f<1>(g, tl, x, coil, AT, Hpart, nchunk, st);
-  if (maxt <= 2) return launch_f<2>(g, tl, x, coil, AT, Hpart, nchunk, st);
-  if (maxt <= 3) return launch_f<3>(g, tl, x, coil, AT, Hpart, nchunk, st);
-  return cudaErrorInvalidValue;
-}
-
-template <int MAXX, int TS>
-static cudaError_t launch_a(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,
-                            const float2* A, float2* xpart, int nchunk, cudaStream_t st) {
-  const int cpc = (g.nc + nchunk - 1) / nchunk;
-  const size_t sm = readout_adj_smem(g, tl.rb, tl.hstage);
-  static int attr = 0;
-  if ((int)sm > attr) {
-    cudaFuncSetAttribute(k1a_tiled<MAXX, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k1a_tiled<MAXX, TS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    attr = (int)sm;
-  }
-  dim3 grid((g.rows + tl.rb - 1) / tl.rb, nchunk);
-  note_launches(1); k1a_tiled<MAXX, TS><<<grid, kRThreads, sm, st>>>(g, tl, H2, coil, A, xpart, cpc);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_k1a_tiled(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,
-                             const float2* A, float2* xpart, int nchunk, cudaStream_t st) {
-  const int mx = ceil_div(tl.rb * g.nx, kRThreads);
-  if (tl.ts == 2) {
-    if (mx <= 1) return launch_a<1, 2>(g, tl, H2, coil, A, xpart, nchunk, st);
-    if (mx <= 2) return launch_a<2, 2>(g, tl, H2, coil, A, xpart, nchunk, st);
-    return cudaErrorInvalidValue;
-  }
-  if (mx <= 1) return launch_a<1, 4>(g, tl, H2, coil, A, xpart, nchunk, st);
-  if (mx <= 2) return launch_a<2, 4>(g, tl, H2, coil, A, xpart, nchunk, st);
-  if (mx <= 4) return launch_a<4, 4>(g, tl, H2, coil, A, xpart, nchunk, st);
-  if (mx <= 8) return launch_a<8, 4>(g, tl, H2, coil, A, xpart, nchunk, st);
-  return cudaErrorInvalidValue;
-}
-
-}  // namespace gpjc
-
-// ====================================================================== batch --
-// Many 2D slices of different sizes and coil counts reconstructed by CG in
-// ONE persistent launch.  Every (slice, stage, tile) is a work item; a
-// global queue hands items out in the order stage-major, then slice, then
-// tile, and each item waits (bounded) until all items of the previous stage
-// of the same slice are done.  Stages per slice: E_c^H S' (phase-encode,
-// readout adjoint, vector init), then per iteration readout forward,
-// phase-encode mask projection with ||E_c p||^2, readout adjoint, and the two
-// CG vector updates.  Dependencies only point to earlier queue positions and
-// all blocks are co-resident (cooperative launch), so the queue cannot
-// deadlock; a wait that exceeds its budget sets the abort flag and every
-// block leaves.
-namespace gpjc {
-
-constexpr int kVecChunk = 2048;  // vector elements per item
-
-enum BatchStage : int { kBPeAdj = 0, kBAdj = 1, kBInit = 2, kBFwd = 3, kBPeN = 4, kBU1 = 5, kBU2 = 6 };
-
-__device__ __forceinline__ int batch_stage_type(int j) {
-  if (j < 3) return j;  // kBPeAdj, kBAdj, kBInit
-  const int k = (j - 3) % 5;
-  return k == 0 ? kBFwd : k == 1 ? kBPeN : k == 2 ? kBAdj : k == 3 ? kBU1 : kBU2;
-}
-
-__device__ __forceinline__ int batch_items(const BatchSlice& s, int type) {
-  switch (type) {
-    case kBPeAdj:
-    case kBPeN: return s.n_pe;
-    case kBAdj: return s.n_a;
-    case kBFwd: return s.n_f;
-    default: return s.n_vec;
-  }
-}
-
-template <bool FWD>
-__device__ __forceinline__ void batch_readout(const BatchSlice& s, const Geo& g, int li, float2* sm) {
-  const int rblock = li / s.nchunk, chunk = li - rblock * s.nchunk;
-  if (FWD) {
-    if (s.mt_f <= 1)
-      k1f_body<1, true>(g, s.rtf, s.p, s.coil, s.AT, s.Hpart, s.cpc, rblock, chunk, sm);
-    else
-      k1f_body<2, true>(g, s.rtf, s.p, s.coil, s.AT, s.Hpart, s.cpc, rblock, chunk, sm);
-  } else {
-    switch (s.mx_a) {
-      case 1: k1a_body<1, true, 4>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
-      case 2: k1a_body<2, true, 4>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
-      case 4: k1a_body<4, true, 4>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
-      case 5: k1a_body<1, true, 2>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
-      case 6: k1a_body<2, true, 2>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
-      default: k1a_body<8, true, 4>(g, s.rta, s.H2, s.coil, s.A, s.xparts, s.cpc, rblock, chunk, sm); break;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kRThreads) k_batch_cg(BatchPlan bp) {
-  extern __shared__ float2 bsm[];
-  __shared__ Geo sg;
-  __shared__ long long s_item;
-  __shared__ int s_ok;
-  __shared__ double red[32];
-  const long long total = bp.stage_start[bp.n_stages];
-  for (;;) {
-    if (threadIdx.x == 0) {
-      long long it = (long long)atomicAdd(bp.head, 1ull);
-      if (*(volatile int*)bp.abort) it = total;
-      s_item = it;
-    }
-    __syncthreads();
-    const long long item = s_item;
-    if (item >= total) break;
-    // decode (stage j, slice s, local item li)
-    int lo = 0, hi = bp.n_stages;  // stage_start[lo] <= item < stage_start[hi]
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (bp.stage_start[mid] <= item) lo = mid; else hi = mid;
-    }
-    const int j = lo, type = batch_stage_type(j);
-    const int* so = bp.slice_off + (size_t)type * (bp.n_slices + 1);
-    const int rem = (int)(item - bp.stage_start[j]);
-    int a = 0, b = bp.n_slices;
-    while (b - a > 1) {
-      const int mid = (a + b) >> 1;
-      if (so[mid] <= rem) a = mid; else b = mid;
-    }
-    const int si = a, li = rem - so[a];
-    const BatchSlice& S = bp.slices[si];
-    // wait for the previous stage of this slice
-    if (threadIdx.x == 0) {
-      int ok = 1;
-      if (j > 0) {
-        const int need = batch_items(S, batch_stage_type(j - 1));
-        volatile int* d = bp.done + (size_t)si * bp.n_stages + (j - 1);
-        const long long t0 = clock64();
-        while (*d < need) {
-          if (*(volatile int*)bp.abort || clock64() - t0 > bp.wait_cycles) {
-            ok = 0;
-            atomicExch(bp.abort, 1);
-            atomicExch(bp.status, (int)kDevTimeout);
-            break;
-          }
-        }
-        __threadfence();
-      }
-      s_ok = ok;
-    }
-    // slice geometry into shared memory
-    {
-      const int* src = reinterpret_cast<const int*>(&S.g);
-      int* dst = reinterpret_cast<int*>(&sg);
-      for (int i = threadIdx.x; i < (int)(sizeof(Geo) / sizeof(int)); i += blockDim.x) dst[i] = __ldg(src + i);
-    }
-    __syncthreads();
-    if (!s_ok) break;
-    const Geo& g = sg;
-    const int iter = j < 3 ? -1 : (j - 3) / 5;
-    const size_t L = (size_t)g.rows * g.nx;
-    switch (type) {
-      case kBPeAdj: pe_adj2d_body(g, S.Sc, g.ntxc, S.H2, li, bsm); break;
-      case kBAdj: batch_readout<false>(S, g, li, bsm); break;
-      case kBFwd: batch_readout<true>(S, g, li, bsm); break;
-      case kBPeN: {
-        const double tot = pe_normal2d_body<true>(g, S.Hpart, S.nchunk, g.ntxc, S.H2, li, bsm);
-        if (threadIdx.x == 0) atomicAdd(S.qq + iter, tot);
-        break;
-      }
-      case kBInit:
-      case kBU1: {
-        double alpha = 0.0;
-        if (type == kBU1) {
-          const double rr = __ldcg(S.rr + iter), qq = __ldcg(S.qq + iter);
-          alpha = rr == 0.0 ? 0.0 : rr / qq;
-          if (!isfinite(alpha)) {
-            if (threadIdx.x == 0) atomicExch(bp.status, (int)kDevNonFinite);
-            alpha = 0.0;
-          }
-        }
-        const float af = (float)alpha;
-        double part = 0.0;
-        const size_t i0 = (size_t)li * kVecChunk, i1 = min(L, i0 + kVecChunk);
-        for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-          float2 v = __ldcg(S.xparts + i);
-          for (int c = 1; c < S.nchunk; ++c) v = cadd(v, __ldcg(S.xparts + c * L + i));
-          if (type == kBInit) {  // b = E_c^H S'; x = 0; r = p = b
-            S.x[i] = make_float2(0.f, 0.f);
-            S.r[i] = v;
-            S.p[i] = v;
-            part += (double)v.x * v.x + (double)v.y * v.y;
-          } else {
-            const float2 pv = __ldcg(S.p + i);
-            float2 xv = __ldcg(S.x + i), rv = __ldcg(S.r + i);
-            xv.x = fmaf(af, pv.x, xv.x);
-            xv.y = fmaf(af, pv.y, xv.y);
-            rv.x = fmaf(-af, v.x, rv.x);
-            rv.y = fmaf(-af, v.y, rv.y);
-            S.x[i] = xv;
-            S.r[i] = rv;
-            part += (double)rv.x * rv.x + (double)rv.y * rv.y;
-          }
-        }
-        const double tot = block_sum(part, red);
-        if (threadIdx.x == 0) atomicAdd(S.rr + (type == kBInit ? 0 : iter + 1), tot);
-        break;
-      }
-      case kBU2: {
-        const double rr = __ldcg(S.rr + iter), rn = __ldcg(S.rr + iter + 1);
-        double beta = rr == 0.0 ? 0.0 : rn / rr;
-        if (!isfinite(beta)) beta = 0.0;
-        const float bf = (float)beta;
-        const size_t i0 = (size_t)li * kVecChunk, i1 = min(L, i0 + kVecChunk);
-        if (rr != 0.0)
-          for (size_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-            const float2 rv = __ldcg(S.r + i);
-            float2 pv = __ldcg(S.p + i);
-            pv.x = fmaf(bf, pv.x, rv.x);
-            pv.y = fmaf(bf, pv.y, rv.y);
-            S.p[i] = pv;
-          }
-        break;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicAdd(bp.done + (size_t)si * bp.n_stages + j, 1);
-    }
-  }
-}
-
-size_t batch_pe_smem(const Geo& g) { return sizeof(float2) * (size_t)(2 * kPeCB * (g.ny + 1) + g.ny); }
-
-cudaError_t launch_batch_cg(const BatchPlan& bp, int grid, size_t smem, cudaStream_t st) {
-  static size_t attr = 0;
-  if (smem > attr) {
-    cudaFuncSetAttribute(k_batch_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_batch_cg, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    attr = smem;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kRThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeCooperative;
-  at[0].val.cooperative = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  note_launches(1);
-  return cudaLaunchKernelEx(&cfg, k_batch_cg, bp);
-}
-
-int batch_max_blocks(size_t smem) {
-  cudaFuncSetAttribute(k_batch_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 0, dev = 0, nsm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cg, kRThreads, smem);
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  return per_sm * nsm;
 }
 
 }  // namespace gpjc
