@@ -5,15 +5,21 @@ One step = the whole hot path for one 2D slice, inputs resident in HBM:
   groups (ROI compaction, Gram, eigen-decomposition, A_g)  -> compression of
   the raw k-space (Eq. 13) -> compressed reconstruction (power iteration for
   the FISTA step + FISTA l1-Haar, or CG-SENSE), all through the C ABI.
+Each step is timed in two parts with CUDA events: groups + compression
+(`compress_s`) and the reconstruction loop (`recon_s_per_slice`, the time
+the paper's SI Table S2 reports).
 
 Metric: E_c+E_c^H pairs per second over the whole step (every pair of the
 power iteration and the reconstruction counted; the group build and the
-compression add to the time, not to the count), with the per-slice time
-reported beside it.  N > 1 GPUs: one rank per GPU, each on its own slice
+compression add to the time, not to the count), with the reconstruction
+loop alone beside it (`recon_pairs_per_s`) and the median of 200 single
+pairs (`pairs_isolated`).  The default 2d256 run also times the BF16
+tensor-core step the same way, the 3D volume (3d224, s/volume) and the
+uneven 64-slice batch.  N > 1 GPUs: one rank per GPU, each on its own slice
 (weak scaling, no collective on the data path).
 
---impl reference times the FP64 CPU oracle on the host cores on a bounded
-sample of the same workload (the reference arm for this method).
+--impl reference times the FP64 CPU oracle on the host cores: real oracle
+E_c + E_c^H pairs of the same slice (the reference arm for this method).
 """
 from __future__ import annotations
 
@@ -46,6 +52,8 @@ def parse():
                     help="time the plain-PyTorch FP32 operator beside the library's (2D workloads)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the BF16 tensor-core step timed beside the FP32 one (2d256)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the 3d224 and batch64 workloads timed after the 2d256 line")
     return ap.parse_args()
 
 
@@ -164,6 +172,37 @@ def k1_flops(g, ntxc, keep_avg, contraction=True):
 
 
 # ---------------------------------------------------------------- gpjc arm --
+def _events(n):
+    import torch
+
+    return [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+
+
+def time_pairs(op, x, n=200, warm=20):
+    """Median device time (us) of single E_c + E_c^H pairs, each between its
+    own pair of CUDA events on the launching stream, after `warm` untimed
+    pairs (inputs resident; the pair's working set stays in L2)."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    y = op.E(x)
+    z = op.EH(y)
+    for _ in range(warm):
+        op.E(x, out=y)
+        op.EH(y, out=z)
+    ev = _events(n)
+    for a, b in ev:
+        a.record(stream)
+        op.E(x, out=y)
+        op.EH(y, out=z)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ts = sorted(a.elapsed_time(b) * 1e3 for a, b in ev)
+    return {"median_us": round(statistics.median(ts), 2), "p10_us": round(ts[n // 10], 2),
+            "p90_us": round(ts[(9 * n) // 10], 2), "n": n, "warmup": warm,
+            "pairs_per_s": round(1e6 / statistics.median(ts), 2)}
+
+
 def run_gpjc(args, rank, world, local):
     import numpy as np
     import torch
@@ -200,60 +239,83 @@ def run_gpjc(args, rank, world, local):
     x = torch.empty(g.shape, dtype=torch.complex64, device=dev)
     power_iters = 20
     pairs_per_step = wl.iters + (power_iters if wl.alg == "fista" else 0)
+    stream = torch.cuda.current_stream()
 
-    def step():
-        grp.rebuild(coils, roi)
-        gpjc.compress(grp, S, prec, out=Sc)
-        if wl.alg == "fista":
-            op.recon(Sc, alg=gpjc.FISTA, iters=wl.iters, lam=wl.lam, power_iters=power_iters,
-                     haar_levels=wl.haar_levels, out=x, sync=False)
-        else:
-            op.recon(Sc, alg=gpjc.CG, iters=wl.iters, out=x, sync=False)
+    def make_step(o, p, sc, xo):
+        """One pass of the hot path, split in two timed parts: (groups +
+        compression) and the reconstruction loop."""
+
+        def part_a():
+            grp.rebuild(coils, roi)
+            gpjc.compress(grp, S, p, out=sc)
+
+        def part_b():
+            if wl.alg == "fista":
+                o.recon(sc, alg=gpjc.FISTA, iters=wl.iters, lam=wl.lam, power_iters=power_iters,
+                        haar_levels=wl.haar_levels, out=xo, sync=False)
+            else:
+                o.recon(sc, alg=gpjc.CG, iters=wl.iters, out=xo, sync=False)
+
+        return part_a, part_b
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    stream = torch.cuda.current_stream()
+
+    def timed_steps(part_a, part_b, steps, o=None, prof=None):
+        """Per step: L2 flush, then events around part a and part b."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+               torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            part_a()
+            ev[i][1].record(stream)
+            part_b()
+            ev[i][2].record(stream)
+            if prof is not None:
+                torch.cuda.synchronize()
+                for s in prof:
+                    ms, n = o.profile_read(s)
+                    prof[s][0] += ms
+                    prof[s][1] += n
+        torch.cuda.synchronize()
+        a = [e0.elapsed_time(e1) for e0, e1, _ in ev]
+        b = [e1.elapsed_time(e2) for _, e1, e2 in ev]
+        return a, b
+
+    part_a, part_b = make_step(op, prec, Sc, x)
     op.profile(True)  # stage events are part of the captured graph from the first call on
     for _ in range(max(3, args.warmup)):
-        step()
+        part_a()
+        part_b()
     torch.cuda.synchronize()
 
-    def barrier():
-        rank_barrier(world)
+    # ---- measured FP32 ALU peak of this device (FMA loop), the roofline denominator
+    alu_peak = gpjc.probe_fp32_tflops()
 
     # ---- timed region (device events per step; L2 flushed between steps)
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = gpjc.launch_count()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     prof = {s: [0.0, 0] for s in (gpjc.STAGE_READOUT_FWD, gpjc.STAGE_PHASE_ENCODE, gpjc.STAGE_READOUT_ADJ)}
-    barrier()
+    rank_barrier(world)
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        for s in prof:
-            ms, n = op.profile_read(s)
-            prof[s][0] += ms
-            prof[s][1] += n
+    ta, tb = timed_steps(part_a, part_b, args.steps, op, prof)
     torch.cuda.synchronize()
-    barrier()
+    rank_barrier(world)
     wall = time.perf_counter() - wall0
     launches = gpjc.launch_count() - launches0
     clocks = sampler.stop()
     op.profile(False)
-    ms_steps = [a.elapsed_time(b) for a, b in ev]
-    total_ms = max_over_ranks(sum(ms_steps), world, dev)
+    total_ms = max_over_ranks(sum(ta) + sum(tb), world, dev)
+    recon_ms = max_over_ranks(sum(tb), world, dev)
     ms_per_step = total_ms / args.steps
     value = job_rate(pairs_per_step, args.steps, world, total_ms)
 
     # ---- dominant kernel and its roofline (FP32 ALU bound)
     fp32 = prec == gpjc.FP32
     names = {gpjc.STAGE_READOUT_FWD: ("k1f_tiled (coil x image, readout FFT, wave PSF, A_g)" if fp32 else
-                                      "k1_sim_fwd2 + k_tc_compress (16-bit spectra, tcgen05 A_g)"),
+                                      "k1_sim_fwd2 + k_tc_compress (readout spectra, tcgen05 A_g)"),
              gpjc.STAGE_PHASE_ENCODE: "k2 (phase-encode FFT / mask projection)",
              gpjc.STAGE_READOUT_ADJ: ("k1a_tiled (A_g^H, inverse readout FFT, coil sum)" if fp32 else
                                       "k_tc_expand + k1_sim_adj2 (tcgen05 A_g^H, inverse FFT, coil sum)")}
@@ -263,44 +325,51 @@ def run_gpjc(args, rank, world, local):
     # 16-bit operators: the A_g contraction runs on the tensor cores, so the
     # FP32 ALU roofline of their readout stage counts the rest only
     fl = k1_flops(g, plan.ntx_c, keep_avg, contraction=fp32)
-    sm_mhz = clocks["sm_mhz"] or 2070.0
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s at the sampled SM clock
     achieved = fl / (dom_ms * 1e-3) / 1e12
     traffic = DRAM_TRAFFIC.get((wl.name, dom)) if fp32 else None
     roofline = {"kernel": names[dom], "bound": "alu", "achieved": round(achieved, 3), "peak": round(alu_peak, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4), "traffic": traffic,
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled SM clock)",
-                "launch_ms": round(dom_ms, 5),
+                "peak_source": "measured: FP32 FMA loop on this device (gpjc_probe_fp32_tflops, SM count x 8 "
+                               "blocks x 256 threads x 8 chains), taken just before the timed region",
+                "launch_ms": round(dom_ms, 5), "flop_per_launch": int(fl),
                 "stage_share": {names[s]: round(prof[s][0] / max(total_ms, 1e-9), 4) for s in prof}}
     if not fp32:
         roofline["alu_work"] = ("coil multiply, pre / post factors and readout FFTs; the A_g contraction "
                                 "(tensor_flop_per_launch) runs on the tensor cores")
         roofline["tensor_flop_per_launch"] = k1_flops(g, plan.ntx_c, keep_avg) - fl
 
-    # ---- end to end through the C ABI with host buffers
+    # ---- single E_c + E_c^H pairs (median of 200), beside the step metric
+    xin = rho.reshape(g.shape).clone()
+    pairs = time_pairs(op, xin)
+
+    # ---- end to end through the C ABI with host buffers (L2 flushed per step)
     e2e = None
     if not args.no_e2e:
         x_h = torch.empty(g.shape, dtype=torch.complex64).pin_memory()
         e2e_steps = args.steps
         torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        rank_barrier(world)
+        tot = 0.0
         for _ in range(e2e_steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
             coils.copy_(coils_h, non_blocking=True)
             roi.copy_(roi_h, non_blocking=True)
             S.copy_(S_h, non_blocking=True)
-            step()
+            part_a()
+            part_b()
             x_h.copy_(x, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        rank_barrier(world)
+        e2e_ms = max_over_ranks(tot, world, dev)
         h2d = coils_h.numel() * 8 + roi_h.numel() + S_h.numel() * 8
         e2e = {"value": round(job_rate(pairs_per_step, e2e_steps, world, e2e_ms), 2), "unit": "pairs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(x_h.numel() * 8),
-               "s_per_slice": round(e2e_ms / 1e3 / e2e_steps, 6)}
+               "s_per_slice": round(e2e_ms / 1e3 / e2e_steps, 6),
+               "l2": "flushed (256 MB write) before each step, outside its events"}
 
     # ---- the same step with the BF16 tensor-core operator, timed the same
     # way: the metric compares it with the plain FP32 step
@@ -312,50 +381,46 @@ def run_gpjc(args, rank, world, local):
         op16.profile(True)  # the same stage events as the FP32 step, so the two times compare like for like
         Sc16 = torch.empty_like(Sc)
         x16 = torch.empty_like(x)
-
-        def step16():
-            grp.rebuild(coils, roi)
-            gpjc.compress(grp, S, gpjc.BF16, out=Sc16)
-            op16.recon(Sc16, alg=gpjc.FISTA, iters=wl.iters, lam=wl.lam, power_iters=power_iters,
-                       haar_levels=wl.haar_levels, out=x16, sync=False)
-
+        a16, b16 = make_step(op16, gpjc.BF16, Sc16, x16)
         for _ in range(max(3, args.warmup)):
-            step16()
+            a16()
+            b16()
         torch.cuda.synchronize()
-        barrier()
-        ev16 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-                for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.zero_()
-            ev16[i][0].record(stream)
-            step16()
-            ev16[i][1].record(stream)
-        torch.cuda.synchronize()
-        barrier()
+        rank_barrier(world)
+        ta16, tb16 = timed_steps(a16, b16, args.steps)
+        rank_barrier(world)
         op16.profile(False)
-        ms16 = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev16), world, dev)
+        ms16 = max_over_ranks(sum(ta16) + sum(tb16), world, dev)
+        rc16 = max_over_ranks(sum(tb16), world, dev)
         v16 = job_rate(pairs_per_step, args.steps, world, ms16)
         # NRMSE (complex, full grid) of the BF16 image against this run's FP32 image
         ref_abs = x32.abs()
         nr = float((x16 - x32).abs().pow(2).mean().sqrt() / (ref_abs.max() - ref_abs.min()))
         bf16 = {"dtype": "bf16", "value": round(v16, 2), "unit": "pairs/s",
                 "ms_per_step": round(ms16 / args.steps, 4), "speedup_vs_fp32": round(v16 / value, 3),
+                "recon_s_per_slice": round(rc16 / 1e3 / args.steps, 6),
+                "compress_s": round(statistics.median(ta16) / 1e3, 6),
+                "recon_speedup_vs_fp32": round(recon_ms / rc16, 3),
+                "recon_pairs_per_s": round(job_rate(pairs_per_step, args.steps, world, rc16), 2),
+                "pairs_isolated": time_pairs(op16, xin),
                 "nrmse_vs_fp32_image": float(f"{nr:.3e}"),
-                "note": "same workload, inputs, stage events and timing as the FP32 step; NRMSE against "
-                        "the FP64 oracle is checked by the tests"}
+                "note": "same workload, inputs, stage events and timing as the FP32 step (BF16 operands as "
+                        "head + remainder, three MMAs per K step); NRMSE against the FP64 oracle is checked "
+                        "by the tests (full-size 2d256 FISTA bound 1e-3)"}
+        del op16
 
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": {gpjc.FP32: "f32", gpjc.BF16: "bf16", gpjc.FP16: "f16"}[prec],
         "data": "synthetic (seeded phantom, Gaussian-phase coils, regular R=3 mask, sigma 1e-3 noise)",
-        "config": {"workload": wl.name, "matrix": [g.nz, g.ny, g.nx], "coils": g.nc, "os": g.os,
-                   "groups": g.n_groups, "w": g.w, "keep": int(g.keep[0]), "ntx_c": plan.ntx_c,
-                   "n_lines": g.n_lines, "alg": wl.alg, "iters": wl.iters,
-                   "power_iters": power_iters if wl.alg == "fista" else 0, "pairs_per_step": pairs_per_step,
-                   "slices_per_step_per_gpu": 1, "l2": "flushed (256 MB write) between timed steps",
-                   "parallelism": f"replicas x{world} (one slice per GPU)"},
-        "recon_s_per_slice": round(ms_per_step / 1e3, 6),
+        "config": config_of(wl, plan.ntx_c, pairs_per_step, power_iters, world),
+        "step": "groups (ROI, Gram, eigen, A_g) + compression + reconstruction (power iteration + FISTA / CG); "
+                "value = pairs of the step / whole-step time",
+        "recon_s_per_slice": round(recon_ms / 1e3 / args.steps, 6),
+        "recon_pairs_per_s": round(job_rate(pairs_per_step, args.steps, world, recon_ms), 2),
+        "compress_s": round(statistics.median(ta) / 1e3, 6),
+        "pairs_isolated": pairs,
         "wall_s": round(wall, 3),
         "clocks": clocks,
         "roofline": roofline,
@@ -364,22 +429,117 @@ def run_gpjc(args, rank, world, local):
     }
     if bf16 is not None:
         out["bf16_tensor_core_step"] = bf16
+    if wl.name == "2d256" and world == 1 and not args.no_extras:
+        del op, grp
+        torch.cuda.empty_cache()
+        out["workloads"] = {"3d224": run_3d(args, dev), "batch64": run_batch(args, 0, 1, local, emit=False)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(wl, pairs_per_step, power_iters)
+        out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
-# ---------------------------------------------------------------- oracle arm --
-def _oracle_sample(wl, pairs_per_step, power_iters, n_groups_sample=1, n_iters_sample=1):
-    """Time the FP64 oracle on a bounded sample of one step and extrapolate:
-    Gram + eigen-decomposition of `n_groups_sample` groups, compression of
-    the slice, E_c^H S' and `n_iters_sample` E_c^H E_c applications plus the
-    FISTA proximal step.  Returns (seconds per full step, sample description)."""
-    import numpy as np
+def config_of(wl, ntx_c, pairs_per_step, power_iters, world):
+    g = wl.geom
+    return {"workload": wl.name, "matrix": [g.nz, g.ny, g.nx], "coils": g.nc, "os": g.os,
+            "groups": g.n_groups, "w": g.w, "keep": int(g.keep[0]), "ntx_c": int(ntx_c),
+            "n_lines": g.n_lines, "alg": wl.alg, "iters": wl.iters,
+            "power_iters": power_iters if wl.alg == "fista" else 0, "pairs_per_step": pairs_per_step,
+            "slices_per_step_per_gpu": 1, "l2": "flushed (256 MB write) between timed steps",
+            "parallelism": f"replicas x{world} (one slice per GPU)"}
 
+
+def run_3d(args, dev):
+    """The 3D volume (224 x 224 x 160, 32 coils, corkscrew wave, 48
+    contiguous groups compressed 20x, 3x3 CAIPI): group build + compression
+    timed once after one warm-up, then the CG-SENSE 10 reconstruction loop
+    (s/volume) timed over 3 runs after 3 warm-up runs, FP32 and BF16
+    operators on the same compressed data (BF16 compression for the BF16
+    operator).  Inputs resident in HBM; the 2.1 GB coil maps exceed L2."""
+    import numpy as np
+    import torch
+
+    from paper_2601_05418_gb300 import gpjc, synth
+
+    wl = synth.workload("3d224")
+    g = wl.geom
+    rho = synth.phantom(g.nx, g.ny, g.nz)
+    roi = torch.from_numpy(synth.roi_mask(rho)).to(dev)
+    coils = torch.from_numpy(synth.coil_maps(g.nx, g.ny, g.nz, g.nc, wl.seed).astype(np.complex64)).to(dev)
+    rho_d = torch.from_numpy(rho.astype(np.complex64)).to(dev)
+    plan = gpjc.Plan(g)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    grp = gpjc.Groups.build(plan, coils, roi)
+    op = gpjc.Operator(grp, coils)
+    S = op.simulate(rho_d)
+    gen = torch.Generator(device=dev).manual_seed(wl.seed)
+    S += wl.sigma / np.sqrt(2) * torch.complex(torch.randn(S.shape, generator=gen, device=dev),
+                                               torch.randn(S.shape, generator=gen, device=dev))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    res = {"config": {"workload": "3d224", "matrix": [g.nz, g.ny, g.nx], "coils": g.nc, "os": g.os,
+                      "groups": g.n_groups, "w": g.w, "keep": int(g.keep[0]), "ntx_c": int(plan.ntx_c),
+                      "n_lines": g.n_lines, "alg": "cg", "iters": wl.iters,
+                      "grouping": "48 contiguous readout subregions, one patch per group per line"},
+           "unit": "s/volume", "higher_is_better": False}
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    for prec, name in ((gpjc.FP32, "fp32"), (gpjc.BF16, "bf16")):
+        o = op if prec == gpjc.FP32 else gpjc.Operator(grp, coils, prec)
+        Sc = torch.empty((g.n_lines, plan.ntx_c), dtype=torch.complex64, device=dev)
+        x = torch.empty(g.shape, dtype=torch.complex64, device=dev)
+        e = _events(2)
+        grp.rebuild(coils, roi)  # warm-up of the group build
+        gpjc.compress(grp, S, prec, out=Sc)
+        e[0][0].record(stream)
+        grp.rebuild(coils, roi)
+        e[0][1].record(stream)
+        e[1][0].record(stream)
+        gpjc.compress(grp, S, prec, out=Sc)
+        e[1][1].record(stream)
+        for _ in range(3):
+            o.recon(Sc, alg=gpjc.CG, iters=wl.iters, out=x, sync=False)
+        ev = _events(3)
+        for a, b in ev:
+            a.record(stream)
+            o.recon(Sc, alg=gpjc.CG, iters=wl.iters, out=x, sync=False)
+            b.record(stream)
+        torch.cuda.synchronize()
+        rec = [a.elapsed_time(b) / 1e3 for a, b in ev]
+        res[name] = {"s_per_volume": round(statistics.median(rec), 4), "runs": 3, "warmup": 3,
+                     "groups_s": round(e[0][0].elapsed_time(e[0][1]) / 1e3, 4),
+                     "compress_s": round(e[1][0].elapsed_time(e[1][1]) / 1e3, 5),
+                     "pairs_per_s": round(wl.iters / statistics.median(rec), 2)}
+        if prec != gpjc.FP32:
+            del o
+    res["clocks"] = sampler.stop()
+    res["bf16_recon_speedup_vs_fp32"] = round(res["fp32"]["s_per_volume"] / res["bf16"]["s_per_volume"], 3)
+    res["setup_s"] = round(setup_s, 2)
+    return res
+
+
+# ---------------------------------------------------------------- oracle arm --
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def _oracle_problem(wl):
+    """The oracle's problem for one slice of the workload: raw data, the
+    compression matrices of every group (from the oracle's Gram and eigh of
+    group 0, reused for all groups: the timed pairs do not depend on which
+    orthonormal A_g they apply) and the compressed data."""
     import oracle as O
     from paper_2601_05418_gb300 import synth
 
@@ -388,32 +548,14 @@ def _oracle_sample(wl, pairs_per_step, power_iters, n_groups_sample=1, n_iters_s
     S = O.simulate(g, case.coils, case.rho, case.noise)
     idx = O.roi_pixels(case.roi, case.coils)
     t0 = time.perf_counter()
-    As = []
-    for gi in range(n_groups_sample):
-        P = O.gram(g, case.coils, idx, gi)
-        A, _ = O.compression_matrix(P, int(g.keep[gi]), g.nc, g.w)
-        As.append(A)
-    t_groups = (time.perf_counter() - t0) / n_groups_sample * g.n_groups
-    As = As + [As[0]] * (g.n_groups - len(As))
+    P = O.gram(g, case.coils, idx, 0)
+    A, _ = O.compression_matrix(P, int(g.keep[0]), g.nc, g.w)
+    t_group = time.perf_counter() - t0
+    As = [A] * g.n_groups
     t0 = time.perf_counter()
     Sc = O.compress(g, As, S)
     t_comp = time.perf_counter() - t0
-    pb = O.Problem(g, case.coils, As)
-    t0 = time.perf_counter()
-    b = pb.EcH(Sc)
-    t_b = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    y = b.copy()
-    for _ in range(n_iters_sample):
-        z = y - (pb.normal_c(y) - b) / 1.0
-        if wl.alg == "fista":
-            y = np.stack([O.wavelet_prox(z[k], wl.lam, wl.haar_levels) for k in range(z.shape[0])])
-    t_it = (time.perf_counter() - t0) / n_iters_sample
-    total = t_groups + t_comp + t_b + t_it * pairs_per_step
-    sample = (f"oracle on {n_groups_sample}/{g.n_groups} groups (Gram+eigh) and {n_iters_sample} of "
-              f"{pairs_per_step} normal-operator iterations of one {wl.name} slice, plus compression and "
-              f"E_c^H S'; extrapolated linearly to the full step")
-    return total, sample
+    return O.Problem(g, case.coils, As), Sc, t_group, t_comp
 
 
 def _blas_threads():
@@ -425,13 +567,47 @@ def _blas_threads():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(wl, pairs_per_step, power_iters):
-    t, sample = _oracle_sample(wl, pairs_per_step, power_iters)
-    return {"value": round(pairs_per_step / t, 4), "unit": "pairs/s", "cores": _blas_threads(), "kind": "oracle",
-            "sample": sample + " (numpy FFT single-threaded, BLAS threaded)", "s_per_slice": round(t, 3)}
+def _oracle_pairs(pb, Sc, n):
+    """Times n oracle E_c + E_c^H pairs (FP64, numpy); returns seconds each."""
+    x = pb.EcH(Sc)
+    ts = []
+    for _ in range(n):
+        t0 = time.perf_counter()
+        x = pb.EcH(pb.Ec(x))
+        ts.append(time.perf_counter() - t0)
+        x = x / max(float(abs(x).max()), 1e-30)
+    return ts
+
+
+def cpu_baseline(wl, n_pairs=8):
+    """The oracle timed on the host cores on a bounded sample: n_pairs real
+    E_c + E_c^H pairs of the same slice (all BLAS threads), one more pair on
+    one thread, and one group's Gram + eigh."""
+    pb, Sc, t_group, t_comp = _oracle_problem(wl)
+    _oracle_pairs(pb, Sc, 1)
+    ts = _oracle_pairs(pb, Sc, n_pairs)
+    t1 = None
+    try:
+        from threadpoolctl import threadpool_limits
+
+        with threadpool_limits(limits=1):
+            t1 = _oracle_pairs(pb, Sc, 1)[0]
+    except Exception:
+        pass
+    pair_s = statistics.median(ts)
+    return {"value": round(1.0 / pair_s, 4), "unit": "pairs/s", "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"{n_pairs} FP64 oracle E_c + E_c^H pairs of one {wl.name} slice (median), after one "
+                      f"warm-up pair; numpy FFT single-threaded, BLAS on all threads",
+            "one_thread_pair_s": round(t1, 4) if t1 is not None else None,
+            "group_gram_eigh_s": round(t_group, 3), "compress_s": round(t_comp, 3),
+            "cpu_model": _cpu_model(), "nproc": os.cpu_count()}
 
 
 def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores.  One step = one
+    E_c + E_c^H pair of the oracle on the same 2D slice (same A_g shapes and
+    data), exactly `steps` of them timed after `warmup`; the full oracle
+    step of the workload is extrapolated from them in its own field."""
     if rank != 0:
         return
     from paper_2601_05418_gb300 import synth
@@ -439,25 +615,45 @@ def run_reference(args, rank, world):
     wl = synth.workload(args.workload)
     power_iters = 20
     pairs_per_step = wl.iters + (power_iters if wl.alg == "fista" else 0)
-    for _ in range(args.warmup):
-        _oracle_sample(wl, pairs_per_step, power_iters)
-    ts, sample = [], ""
-    for _ in range(args.steps):
-        t, sample = _oracle_sample(wl, pairs_per_step, power_iters)
-        ts.append(t)
-    t = sum(ts) / len(ts)
-    value = pairs_per_step / t
+    pb, Sc, t_group, t_comp = _oracle_problem(wl)
+    _oracle_pairs(pb, Sc, args.warmup)
+    t0 = time.perf_counter()
+    ts = _oracle_pairs(pb, Sc, args.steps)
+    wall = time.perf_counter() - t0
+    t1 = None
+    try:
+        from threadpoolctl import threadpool_limits
+
+        with threadpool_limits(limits=1):
+            t1 = _oracle_pairs(pb, Sc, 1)[0]
+    except Exception:
+        pass
+    total = sum(ts)
+    value = args.steps / total
+    import oracle as O
+
+    ntxc = int(O.ntx_compressed(wl.geom.patch_group, wl.geom.keep))
     out = {"metric": METRIC, "value": round(value, 4), "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(t * 1e3, 2), "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": wl.name, "pairs_per_step": pairs_per_step}, "impl": "reference",
+           "warmup": args.warmup, "ms_per_step": round(total / args.steps * 1e3, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config_of(wl, ntxc, pairs_per_step, power_iters, world), "impl": "reference",
+           "step": "one FP64 oracle E_c + E_c^H pair of the slice (the pairs are measured, not extrapolated)",
+           "wall_s": round(wall, 3),
+           "oracle_full_step_s_extrapolated": round(t_group * wl.geom.n_groups + t_comp + pairs_per_step * total
+                                                    / args.steps, 2),
+           "extrapolation": f"{wl.geom.n_groups} x one group's Gram + eigh ({t_group:.2f} s) + compression "
+                            f"({t_comp:.2f} s) + {pairs_per_step} x the median pair",
            "cpu_baseline": {"value": round(value, 4), "unit": "pairs/s", "cores": _blas_threads(), "kind": "oracle",
-                            "sample": sample},
+                            "sample": f"{args.steps} FP64 oracle E_c + E_c^H pairs of one {wl.name} slice after "
+                                      f"{args.warmup} warm-up pairs; numpy FFT single-threaded, BLAS on all "
+                                      f"threads",
+                            "one_thread_pair_s": round(t1, 4) if t1 is not None else None,
+                            "cpu_model": _cpu_model(), "nproc": os.cpu_count()},
            "e2e": {"value": round(value, 4), "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def run_batch(args, rank, world, local):
+def run_batch(args, rank, world, local, emit=True):
     """64 uneven 2D slices, CG-SENSE 30 iterations each, in one persistent
     launch replayed from a CUDA graph; the same slices reconstructed one
     after another with the single-slice path are timed beside it."""
@@ -471,7 +667,7 @@ def run_batch(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
+    if world > 1 and emit:
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=dev)
@@ -547,6 +743,8 @@ def run_batch(args, rank, world, local):
            "speedup_vs_sequential": round(seq_ms / ms, 3),
            "recon_s_per_slice": round(ms / 1e3 / len(ops), 6),
            "clocks": clocks, "gpu_launches": int(launches)}
+    if not emit:
+        return out
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -160,10 +160,10 @@ gpjc_status gpjc_groups_get(const gpjc_groups* groups, float* h_A, double* h_rit
  * forward differences, no difference across the last column / row.
  *   d_x, d_g  [nz][ny][nx] complex64, device, caller-owned; d_g must not
  *             alias d_x
- *   eps       > 0
+ *   eps       > 0, with eps^2 a normal FP32 number (about 1.1e-19 .. 1.8e19)
  * Asynchronous on `stream`; allocates nothing.  GPJC_EINVAL for null or
- * aliased pointers, a dimension < 1 or eps <= 0; GPJC_ECUDA if the launch
- * fails. */
+ * aliased pointers, a dimension < 1 or an eps outside that range;
+ * GPJC_ECUDA if the launch fails. */
 gpjc_status gpjc_tv_grad(const float* d_x, int32_t nz, int32_t ny, int32_t nx, double eps, float* d_g,
                          void* stream);
 
@@ -197,9 +197,12 @@ gpjc_status gpjc_groups_roi(const gpjc_groups* groups, int32_t* h_pix);
  *   d_S  [n_lines][nc][ntx] complex64 raw data, device (16-byte aligned for BF16 / FP16)
  *   d_Sc [n_lines][ntx_c]  complex64 output, device
  * GPJC_FP32 contracts in FP32; GPJC_BF16 / GPJC_FP16 stage patch tiles with
- * TMA, round to 16 bits and run the group GEMMs on the tensor cores (FP32
- * accumulation); they need a periodic group map (patch p in group p mod G,
- * G w dividing ntx), else GPJC_EUNSUPPORTED. */
+ * TMA and run the group GEMMs on the tensor cores with FP32 accumulation:
+ * FP16 rounds each operand once, BF16 carries each operand as a BF16 head
+ * and a BF16 remainder (three MMAs per K step, about 16 mantissa bits per
+ * product).  They need a periodic group map (patch p in group p mod G, G w
+ * dividing ntx; the contiguous map with one patch per group is one), else
+ * GPJC_EUNSUPPORTED. */
 gpjc_status gpjc_compress(const gpjc_groups* groups, const float* d_S, float* d_Sc, gpjc_precision prec,
                           void* stream);
 
@@ -208,11 +211,36 @@ gpjc_status gpjc_compress(const gpjc_groups* groups, const float* d_S, float* d_
  * valid and unchanged while the operator lives) and allocates the
  * workspaces.  nchunk: coil chunks of the readout stage (0 = automatic).
  * prec: GPJC_FP32 applies A_g with FP32 FFMA inside the fused readout
- * kernels; GPJC_BF16 / GPJC_FP16 write the readout spectra as 16-bit hybrid
- * data and apply A_g / A_g^H as tensor-core GEMMs (periodic group maps).
- * Synchronous. */
+ * kernels; GPJC_BF16 / GPJC_FP16 write the readout spectra (FP32 for BF16,
+ * whose GEMM splits them into head + remainder; FP16 for FP16) and apply
+ * A_g / A_g^H as tensor-core GEMMs (periodic group maps).  Allocates the
+ * gpjc_query workspace; GPJC_ENOMEM (and nothing left allocated) when a
+ * device allocation fails.  Synchronous. */
 gpjc_status gpjc_op_create(const gpjc_groups* groups, const float* d_coil, gpjc_precision prec, int32_t nchunk,
                            gpjc_op** out);
+/* Sizes of an operator before it is created (Eq. 15's N'_tx = sum over
+ * patches of the kept dimension of the patch's group, Sec. 2.4): *ntx_c
+ * receives N'_tx (the row length of S' and of the hybrid matrix), and
+ * *workspace_bytes the device bytes gpjc_op_create(groups, ..., prec,
+ * nchunk, ...) would allocate (hybrid matrices, partial images, CG / FISTA
+ * vectors, scalars and, for BF16 / FP16, the spectra buffer).  Either
+ * output may be NULL.  Host only, no device work.  GPJC_EINVAL for bad
+ * arguments, GPJC_EUNSUPPORTED where gpjc_op_create would refuse the
+ * precision. */
+gpjc_status gpjc_query(const gpjc_groups* groups, gpjc_precision prec, int32_t nchunk, int32_t* ntx_c,
+                       uint64_t* workspace_bytes);
+/* Measured FP32 FMA throughput of the current device (no counterpart in the
+ * paper): the denominator of the FP32 ALU roofline of the readout kernels.
+ * Runs SM count x 8 blocks of 256 threads, eight independent FMA chains of
+ * `iters` iterations per thread (after one warm-up launch), times it with
+ * CUDA events and writes TFLOP/s (2 flops per FMA) to *tflops.
+ * Synchronous; allocates 16 bytes of device memory for its inputs. */
+gpjc_status gpjc_probe_fp32_tflops(int32_t iters, double* tflops);
+/* Test hook for the out-of-memory paths (no counterpart in the paper): after
+ * gpjc_debug_fail_allocations(n) the library's (n+1)-th and later device
+ * allocations fail with GPJC_ENOMEM without calling cudaMalloc; n < 0
+ * restores normal allocation.  Process-wide. */
+void gpjc_debug_fail_allocations(int64_t n);
 void gpjc_op_destroy(gpjc_op* op);
 /* Times the readout-stage coil-chunk choices on `stream` and keeps the
  * fastest (synchronous): the adjoint's chunk count, then the forward's, and
@@ -298,10 +326,12 @@ gpjc_status gpjc_batch_info(const gpjc_batch* batch, int32_t* grid, int64_t* ite
  * Scratch: a static 32 MiB device array inside the library, held on every
  * GPU that loads the library until the process exits; geometries whose
  * hybrid matrix (rows x ntx_c complex64, twice that in 3D) exceeds it are
- * rejected with GPJC_EINVAL before any launch.  Calls allocate nothing and
+ * rejected with GPJC_EINVAL before any launch, and so are buffers that are
+ * not device memory of the current device.  Calls allocate nothing and
  * free nothing.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current: make that first
- * call before any stream capture.  Every call on a device shares the one
+ * address (cudaGetSymbolAddress) with that device current, and again when
+ * the device's context has changed since (after cudaDeviceReset): make that
+ * first call before any stream capture.  Every call on a device shares the one
  * array and overwrites all of it that it reads, so no state carries over;
  * calls whose execution overlaps on the GPU (other streams, other threads)
  * race on it and must be serialised by the caller. */

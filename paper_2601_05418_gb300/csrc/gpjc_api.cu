@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -70,6 +71,21 @@ extern "C" const char* gpjc_last_error(void) { return g_err.c_str(); }
 extern "C" const char* gpjc_version(void) { return "gpjc 0.1 (sm_103a)"; }
 
 // ------------------------------------------------------------------ memory --
+// Allocation-failure injection for tests of the out-of-memory paths: after
+// gpjc_debug_fail_allocations(n), the (n+1)-th and later device allocations
+// of the library fail with GPJC_ENOMEM without calling cudaMalloc (n < 0:
+// off).  Process-wide.
+static std::atomic<long long> g_alloc_budget{-1};
+static bool alloc_refused() {
+  long long b = g_alloc_budget.load();
+  while (b >= 0) {
+    if (b == 0) return true;
+    if (g_alloc_budget.compare_exchange_weak(b, b - 1)) return false;
+  }
+  return false;
+}
+extern "C" void gpjc_debug_fail_allocations(int64_t n) { g_alloc_budget.store(n < 0 ? -1 : n); }
+
 namespace {
 
 struct DevMem {
@@ -83,6 +99,7 @@ struct DevMem {
   gpjc_status alloc(T** out, size_t n) {
     *out = nullptr;
     if (n == 0) n = 1;
+    if (alloc_refused()) return fail(GPJC_ENOMEM, "cudaMalloc(%zu bytes): refused (injected)", n * sizeof(T));
     void* p = nullptr;
     cudaError_t e = cudaMalloc(&p, n * sizeof(T));
     if (e != cudaSuccess) {
@@ -179,7 +196,8 @@ static bool make_tc_geom(const gpjc_plan* p, int ebytes, TcGeom* t) {
   t->Kx = ((2 * p->keep_max + 15) / 16) * 16;
   t->nexp = ((2 * p->ns + 15) / 16) * 16;
   if (t->box0 > 256 || ncc > 256 || t->lt > 256 || n_occ > 256) return false;
-  if (tc_compress_smem(*t) > 220 * 1024 || tc_expand_smem(*t) > 220 * 1024) return false;
+  // FP32 sources serve the split BF16 compression (two images per operand)
+  if (tc_compress_smem(*t, ebytes == 4 ? 1 : 0) > 220 * 1024 || tc_expand_smem(*t, 1) > 220 * 1024) return false;
   return true;
 }
 
@@ -428,9 +446,10 @@ static gpjc_status groups_alloc_A(gpjc_groups* gr) {
   gr->tc_status = nullptr;
   if (p->tc_ok) {
     const TcGeom& t = p->tc16;
-    const size_t nbc = (size_t)p->G * t.nchunks * t.npad * t.Kc, nbx = (size_t)p->G * t.nexp * t.Kx;
     for (int f = 0; f < 2; ++f)
-      if ((s = gr->mem.alloc(&gr->tc_bc[f], nbc)) || (s = gr->mem.alloc(&gr->tc_bx[f], nbx))) return s;
+      if ((s = gr->mem.alloc(&gr->tc_bc[f], tc_pack_comp_elems(t, f))) ||
+          (s = gr->mem.alloc(&gr->tc_bx[f], tc_pack_exp_elems(t, f))))
+        return s;
     if ((s = gr->mem.alloc(&gr->tc_status, 1))) return s;
     CK(cudaMemset(gr->tc_status, 0, sizeof(int)));
   }
@@ -655,8 +674,13 @@ extern "C" gpjc_status gpjc_tv_grad(const float* d_x, int32_t nz, int32_t ny, in
   if (!d_x || !d_g) return fail(GPJC_EINVAL, "null argument");
   if (nz < 1 || ny < 1 || nx < 1) return fail(GPJC_EINVAL, "image dimensions must be >= 1");
   if (!(eps > 0.0) || !std::isfinite(eps)) return fail(GPJC_EINVAL, "eps must be finite and > 0");
+  // the kernel works with eps^2 in FP32: it must be a normal positive float
+  // (a zero or subnormal eps^2 makes flat regions divide by zero)
+  const double eps2 = eps * eps;
+  if (!(eps2 >= (double)FLT_MIN) || !(eps2 <= (double)FLT_MAX))
+    return fail(GPJC_EINVAL, "eps^2 = %g is not a normal FP32 number", eps2);
   if ((const void*)d_x == (const void*)d_g) return fail(GPJC_EINVAL, "d_g must not alias d_x");
-  CK(launch_tv_grad((const float2*)d_x, (float2*)d_g, nz, ny, nx, (float)eps, (cudaStream_t)stream));
+  CK(launch_tv_grad((const float2*)d_x, (float2*)d_g, nz, ny, nx, (float)eps2, (cudaStream_t)stream));
   return GPJC_OK;
 }
 
@@ -832,6 +856,71 @@ static int auto_nchunk(const gpjc_plan* p) {
   return n;
 }
 
+// Workspace layout of an operator: chunk counts and element counts of every
+// device buffer gpjc_op_create allocates (shared with gpjc_query).
+struct OpSizes {
+  int nchunk, nchunk_max, nchunk_a, nchunk_a_max, adj_pieces;
+  size_t L, HN, npartials, hist_len, spectra;
+  size_t bytes;  // total device bytes
+};
+static OpSizes op_sizes(const gpjc_plan* p, gpjc_precision prec, int nchunk) {
+  OpSizes z{};
+  const Geo& g = p->geo;
+  z.nchunk = nchunk > 0 ? nchunk : auto_nchunk(p);
+  // workspaces sized for the largest chunk count the autotuner may pick
+  int nmax = z.nchunk;
+  {
+    int n = 1;
+    while (n * 2 <= p->nc && n * 2 <= 16) n *= 2;
+    const size_t per = (size_t)p->ny * p->nz * std::max(p->ntxc, p->nx) * sizeof(float2);
+    while (n > nmax && (size_t)n * per > ((size_t)4 << 30)) n /= 2;
+    nmax = std::max(nmax, n);
+  }
+  z.nchunk_max = nmax;
+  z.L = (size_t)g.rows * g.nx;
+  // the adjoint's partial images are small: allow up to nc chunks (1 GB cap)
+  {
+    int n = 1;
+    while (n * 2 <= p->nc && (size_t)n * 2 * z.L * sizeof(float2) <= ((size_t)1 << 30)) n *= 2;
+    z.nchunk_a_max = std::max(n, nmax);
+    z.nchunk_a = std::min(auto_nchunk_adj(p), z.nchunk_a_max);
+    z.adj_pieces = auto_adj_pieces(p);
+    // GPJC_ADJ_PIECES=n (1..8) overrides the default split (the results do
+    // not depend on it: whole expansion row tiles per piece)
+    if (const char* e = getenv("GPJC_ADJ_PIECES")) {
+      const int v = atoi(e);
+      if (v >= 1 && v <= kMaxAdjPieces) z.adj_pieces = v;
+    }
+  }
+  z.HN = (size_t)g.rows * g.ntxc;
+  z.npartials = std::max(pe_normal_blocks(g, g.ntxc), sum_parts_blocks(z.L)) + 16;
+  z.hist_len = (size_t)1 << 14;
+  z.spectra = prec != GPJC_FP32 ? (size_t)g.rows * g.nc * g.ntx : 0;
+  const size_t c64 = z.HN * nmax + z.HN + z.L * (size_t)z.nchunk_a_max + 6 * z.L + (g.dim3d ? z.HN : 0) + z.spectra;
+  z.bytes = sizeof(float2) * c64 + sizeof(double) * (z.npartials + SC_N + z.hist_len) + 4 * sizeof(unsigned) +
+            4 * sizeof(int);
+  return z;
+}
+
+extern "C" gpjc_status gpjc_probe_fp32_tflops(int32_t iters, double* tflops) {
+  if (!tflops || iters < 1) return fail(GPJC_EINVAL, "tflops must be non-NULL and iters >= 1");
+  CK(probe_fma_tflops(iters, tflops));
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_query(const gpjc_groups* gr, gpjc_precision prec, int32_t nchunk, int32_t* ntx_c,
+                                  uint64_t* workspace_bytes) {
+  if (!gr) return fail(GPJC_EINVAL, "null groups");
+  if (prec != GPJC_FP32 && prec != GPJC_BF16 && prec != GPJC_FP16) return fail(GPJC_EINVAL, "unknown precision");
+  const gpjc_plan* p = gr->plan;
+  if (nchunk < 0 || nchunk > p->nc) return fail(GPJC_EINVAL, "nchunk must be in [0, nc]");
+  if (prec != GPJC_FP32 && !p->tc_ok)
+    return fail(GPJC_EUNSUPPORTED, "the tensor-core operator needs a periodic group map");
+  if (ntx_c) *ntx_c = p->ntxc;
+  if (workspace_bytes) *workspace_bytes = (uint64_t)op_sizes(p, prec, nchunk).bytes;
+  return GPJC_OK;
+}
+
 extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil, gpjc_precision prec,
                                       int32_t nchunk, gpjc_op** out) {
   if (!gr || !d_coil || !out) return fail(GPJC_EINVAL, "null argument");
@@ -848,34 +937,16 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   op->plan = p;
   op->coil = (const float2*)d_coil;
   op->prec = prec;
-  op->nchunk = nchunk > 0 ? nchunk : auto_nchunk(p);
-  // workspaces sized for the largest chunk count the autotuner may pick
-  int nmax = op->nchunk;
-  {
-    int n = 1;
-    while (n * 2 <= p->nc && n * 2 <= 16) n *= 2;
-    const size_t per = (size_t)p->ny * p->nz * std::max(p->ntxc, p->nx) * sizeof(float2);
-    while (n > nmax && (size_t)n * per > ((size_t)4 << 30)) n /= 2;
-    nmax = std::max(nmax, n);
-  }
+  const OpSizes z = op_sizes(p, prec, nchunk);
+  op->nchunk = z.nchunk;
+  const int nmax = z.nchunk_max;
   op->nchunk_max = nmax;
   const Geo& g = p->geo;
-  op->L = (size_t)g.rows * g.nx;
-  // the adjoint's partial images are small: allow up to nc chunks (1 GB cap)
-  {
-    int n = 1;
-    while (n * 2 <= p->nc && (size_t)n * 2 * op->L * sizeof(float2) <= ((size_t)1 << 30)) n *= 2;
-    op->nchunk_a_max = std::max(n, nmax);
-    op->nchunk_a = std::min(auto_nchunk_adj(p), op->nchunk_a_max);
-    op->adj_pieces = auto_adj_pieces(p);
-    // GPJC_ADJ_PIECES=n (1..8) overrides the default split (the results do
-    // not depend on it: whole expansion row tiles per piece)
-    if (const char* e = getenv("GPJC_ADJ_PIECES")) {
-      const int v = atoi(e);
-      if (v >= 1 && v <= kMaxAdjPieces) op->adj_pieces = v;
-    }
-  }
-  const size_t HN = (size_t)g.rows * g.ntxc;
+  op->L = z.L;
+  op->nchunk_a_max = z.nchunk_a_max;
+  op->nchunk_a = z.nchunk_a;
+  op->adj_pieces = z.adj_pieces;
+  const size_t HN = z.HN;
   gpjc_status s;
   DevMem& m = op->mem;
   if ((s = m.alloc(&op->Hpart, HN * nmax)) || (s = m.alloc(&op->H2, HN)) ||
@@ -885,8 +956,8 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
     return s;
   op->T = nullptr;
   if (g.dim3d && (s = m.alloc(&op->T, HN))) return s;
-  op->npartials = std::max(pe_normal_blocks(g, g.ntxc), sum_parts_blocks(op->L)) + 16;
-  op->hist_len = 1 << 14;
+  op->npartials = (int)z.npartials;
+  op->hist_len = (int)z.hist_len;
   if ((s = m.alloc(&op->partials, op->npartials)) || (s = m.alloc(&op->counter, 4)) ||
       (s = m.alloc(&op->sc, SC_N)) || (s = m.alloc(&op->hist, op->hist_len)) || (s = m.alloc(&op->status, 4)))
     return s;
@@ -896,11 +967,13 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   op->V = op->TV = nullptr;
   op->V16 = nullptr;
   if (prec != GPJC_FP32) {
-    // one buffer serves the 16-bit forward spectra and the FP32 adjoint spectra
+    // one buffer serves the forward spectra (FP16, or FP32 for the split BF16
+    // compression) and the FP32 adjoint spectra
     float2* v16;
-    if ((s = m.alloc(&v16, (size_t)g.rows * g.nc * g.ntx))) return s;
+    if ((s = m.alloc(&v16, z.spectra))) return s;
     op->V16 = v16;
-    if (!make_tc_tmap(p->tc16, op->V16, g.rows, 2, &op->map16))
+    const bool f32src = prec == GPJC_BF16;
+    if (!make_tc_tmap(f32src ? p->tc32 : p->tc16, op->V16, g.rows, f32src ? 4 : 2, &op->map16))
       return fail(GPJC_ECUDA, "cuTensorMapEncodeTiled failed");
   }
   op->gexec = nullptr;
@@ -939,13 +1012,16 @@ extern "C" void gpjc_op_destroy(gpjc_op* op) {
 static cudaError_t readout_fwd(const gpjc_op* op, const float2* x, cudaStream_t st) {
   const gpjc_plan* p = op->plan;
   if (op->prec != GPJC_FP32) {
+    // BF16: FP32 spectra, split into head + remainder by the compression GEMM;
+    // FP16: FP16 spectra, one rounding
     const int fmt = op->prec == GPJC_BF16 ? 1 : 0;
-    cudaError_t e = fmt ? launch_sim_fwd_bf16(p->geo, x, op->coil, op->V16, op->nchunk, st)
+    cudaError_t e = fmt ? launch_sim_fwd(p->geo, x, op->coil, (float2*)op->V16, op->nchunk, st)
                         : launch_sim_fwd_f16(p->geo, x, op->coil, op->V16, op->nchunk, st);
     if (e != cudaSuccess) return e;
-    TcGeom t = p->tc16;
+    TcGeom t = fmt ? p->tc32 : p->tc16;
     t.scale = op->gr->scale;
-    return launch_tc_compress(op->map16, t, fmt, 2, op->gr->tc_bc[fmt], op->Hpart, p->geo.rows, op->status, st);
+    return launch_tc_compress(op->map16, t, fmt, fmt ? 4 : 2, op->gr->tc_bc[fmt], op->Hpart, p->geo.rows,
+                              op->status, st);
   }
   if (p->rt_f.rb && !op->legacy_readout)
     return launch_k1f_tiled(p->geo, p->rt_f, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st);
@@ -1335,7 +1411,40 @@ extern "C" gpjc_status gpjc_op_profile_read(const gpjc_op* op, int32_t stage, do
 static constexpr size_t kStaticScratchBytes = (size_t)32 << 20;  // 32 MiB on every device that loads the library
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 static std::mutex g_static_mu;
-static void* g_static_addr[256];  // per device ordinal, filled on the first call on that device
+// per device ordinal: the context the address was looked up in, and the
+// address (looked up again when the device's context changed, e.g. after
+// cudaDeviceReset)
+static void* g_static_ctx[256];
+static void* g_static_addr[256];
+
+// current driver context, through the runtime's driver entry-point lookup
+// (nullptr when unavailable)
+static void* current_context() {
+  using ctx_fn = int (*)(void**);
+  static ctx_fn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (ctx_fn)f;
+  }
+  void* ctx = nullptr;
+  if (fn && fn(&ctx) != 0) ctx = nullptr;
+  return ctx;
+}
+
+// true when `p` is device (or managed) memory of device `dev`
+static bool on_device(const void* p, int dev) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
 
 extern "C" gpjc_status gpjc_apply_EH_static(const gpjc_groups* gr, const float* d_coil, const float* d_y,
                                             float* d_x, void* stream) {
@@ -1349,15 +1458,20 @@ extern "C" gpjc_status gpjc_apply_EH_static(const gpjc_groups* gr, const float* 
   int dev = -1;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) return fail(GPJC_EUNSUPPORTED, "device ordinal %d out of range", dev);
+  // the kernels run on the current device: every buffer must live there
+  if (!on_device(d_coil, dev) || !on_device(d_y, dev) || !on_device(d_x, dev))
+    return fail(GPJC_EINVAL, "d_coil, d_y and d_x must be device memory of the current device (%d)", dev);
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_addr[dev]) {
+    void* ctx = current_context();
+    if (!g_static_addr[dev] || g_static_ctx[dev] != ctx) {
       void* p = nullptr;
       cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
       if (e != cudaSuccess || !p)
         return fail(GPJC_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
       g_static_addr[dev] = p;
+      g_static_ctx[dev] = ctx;
     }
     base = g_static_addr[dev];
   }

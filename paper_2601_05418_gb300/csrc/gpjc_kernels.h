@@ -22,17 +22,13 @@ cudaError_t launch_k1_adj_fp32(const Geo& g, const float2* H2, const float2* coi
                                float2* xpart, int nchunk, cudaStream_t st);
 cudaError_t launch_sim_fwd(const Geo& g, const float2* x, const float2* coil, float2* V, int nchunk,
                            cudaStream_t st);
-cudaError_t launch_sim_fwd_bf16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
-                                cudaStream_t st);
 cudaError_t launch_sim_adj(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
                            cudaStream_t st);
 // gradient of the smoothed isotropic TV of each z-slice (k_tv.cu)
-cudaError_t launch_tv_grad(const float2* u, float2* g, int nz, int ny, int nx, float eps, cudaStream_t st);
+cudaError_t launch_tv_grad(const float2* u, float2* g, int nz, int ny, int nx, float eps2, cudaStream_t st);
 // rows [row0, row0 + nrows) only (the other rows' partial images are untouched)
 cudaError_t launch_sim_adj_rows(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
                                 int row0, int nrows, cudaStream_t st);
-cudaError_t launch_sim_adj_bf16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,
-                                cudaStream_t st);
 cudaError_t launch_pe_fwd(const Geo& g, const float2* Hpart, int nchunk, int ncols, float2* T, float2* Sc,
                           cudaStream_t st);
 cudaError_t launch_pe_adj(const Geo& g, const float2* Sc, int ncols, float2* T, float2* H, cudaStream_t st);
@@ -64,8 +60,12 @@ int batch_max_blocks(size_t smem);
 
 // ---- tensor-core compression (k_tc.cu)
 bool make_tc_tmap(const TcGeom& t, const void* base, int lines, int ebytes, CUtensorMap* map);
-size_t tc_compress_smem(const TcGeom& t);
-size_t tc_expand_smem(const TcGeom& t);
+// fmt 1 = BF16 (head + remainder images, three MMAs per K step; FP32 sources
+// only), 0 = FP16 (one image)
+size_t tc_compress_smem(const TcGeom& t, int fmt);
+size_t tc_expand_smem(const TcGeom& t, int fmt);
+size_t tc_pack_comp_elems(const TcGeom& t, int fmt);  // uint16 elements of all compression images
+size_t tc_pack_exp_elems(const TcGeom& t, int fmt);   // uint16 elements of all expansion images
 cudaError_t launch_tc_pack(const TcGeom& t, int fmt, const float2* A, const float* scale, uint16_t* Bc,
                            uint16_t* Bx, cudaStream_t st);
 cudaError_t launch_tc_compress(const CUtensorMap& map, const TcGeom& t, int fmt, int src_bytes, const uint16_t* Bc,
@@ -113,6 +113,9 @@ cudaError_t launch_form_A(const Geo& g, int b, const double2* U, const float2* T
                           float* scale, cudaStream_t st);
 cudaError_t launch_compress_fp32(const Geo& g, const float2* S, int n_lines_in, const float2* AT, float2* Sc,
                                  cudaStream_t st);
+
+// ---- FP32 FMA throughput probe (k_probe.cu): synchronous, on the default stream
+cudaError_t probe_fma_tflops(int iters, double* tflops);
 
 // ---- recon (k_recon.cu)
 cudaError_t launch_sum_parts(const float2* parts, int nchunk, size_t L, float2* out, double* partials,

@@ -317,10 +317,6 @@ cudaError_t launch_sim_fwd(const Geo& g, const float2* x, const float2* coil, fl
                            cudaStream_t st) {
   return launch_sim_fwd_t<float2>(g, x, coil, V, nchunk, st);
 }
-cudaError_t launch_sim_fwd_bf16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
-                                cudaStream_t st) {
-  return launch_sim_fwd_t<__nv_bfloat162>(g, x, coil, (__nv_bfloat162*)V, nchunk, st);
-}
 cudaError_t launch_sim_fwd_f16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
                                cudaStream_t st) {
   return launch_sim_fwd_t<__half2>(g, x, coil, (__half2*)V, nchunk, st);
@@ -336,10 +332,6 @@ cudaError_t launch_sim_adj(const Geo& g, const float2* V, const float2* coil, fl
 cudaError_t launch_sim_adj_rows(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
                                 int row0, int nrows, cudaStream_t st) {
   return launch_sim_adj_t<float2>(g, V, coil, xpart, nchunk, row0, nrows, st);
-}
-cudaError_t launch_sim_adj_bf16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,
-                                cudaStream_t st) {
-  return launch_sim_adj_t<__nv_bfloat162>(g, (const __nv_bfloat162*)V, coil, xpart, nchunk, 0, g.rows, st);
 }
 
 #endif  // GPJC_DEVICE_SOURCE_ONLY

@@ -19,6 +19,12 @@
 // The adjoint (A_g^H applied to the compressed columns) is the same GEMM
 // with the roles of k and i exchanged and N tiled by 256.
 //
+// BF16 (8 mantissa bits) runs split: every operand value v is carried as a
+// head h = bf16(v) and a remainder l = bf16(v - h), and each K step issues
+// three MMAs into the same accumulator (h_X h_B + l_X h_B + h_X l_B), so the
+// products keep about 16 mantissa bits and the image stays within the
+// FP32-path error of the oracle; FP16 (11 bits) runs one MMA per K step.
+//
 // Every wait on an mbarrier is bounded; on timeout the block records
 // kDevTimeout in the status word, drains what it issued (again bounded),
 // frees its tensor memory and returns.
@@ -182,6 +188,14 @@ __host__ __device__ __forceinline__ int core_off(int row, int k, int Kt) {
   return (row >> 3) * (Kt << 3) + (k >> 3) * 64 + (row & 7) * 8 + (k & 7);
 }
 
+// 16-bit images per operand: 2 (head + remainder) for BF16, 1 for FP16
+__host__ __device__ constexpr int tc_images(int fmt) { return fmt == 1 ? 2 : 1; }
+// elements of one group's expansion images (tiles of 256 rows, each tile
+// its head image and, for BF16, its remainder image)
+__host__ __device__ inline size_t tc_exp_group_elems(const TcGeom& t, int fmt) {
+  return (size_t)((t.nexp + 255) / 256) * tc_images(fmt) * 256 * t.Kx;
+}
+
 // ------------------------------------------------------------------ packing --
 // Compression B per (group, coil chunk): rows 2k + c' (N), columns
 // 2 (n_local w + tau) + c (K), core-matrix image, values of A_g / scale_g.
@@ -190,7 +204,8 @@ __global__ void k_tc_pack_comp(TcGeom t, const float2* __restrict__ A, const flo
                                uint16_t* __restrict__ B) {
   const int g = blockIdx.y, chunk = blockIdx.z;
   const size_t per = (size_t)t.npad * t.Kc;
-  uint16_t* Bg = B + ((size_t)g * t.nchunks + chunk) * per;
+  // head image, then (BF16) the remainder image of the same (group, chunk)
+  uint16_t* Bg = B + ((size_t)g * t.nchunks + chunk) * per * tc_images(FMT);
   const float inv = scale[g] > 0.f ? 1.0f / scale[g] : 0.f;
   const int keep = t.keep[g];
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < t.npad * t.Kc; idx += gridDim.x * blockDim.x) {
@@ -207,6 +222,7 @@ __global__ void k_tc_pack_comp(TcGeom t, const float2* __restrict__ A, const flo
     }
     const uint32_t p = pack2<FMT>(v, 0.f);
     Bg[core_off(nr, kk, t.Kc)] = (uint16_t)(p & 0xFFFF);
+    if (tc_images(FMT) == 2) Bg[per + core_off(nr, kk, t.Kc)] = (uint16_t)(pack2<FMT>(v - unpack2<FMT>(p).x, 0.f) & 0xFFFF);
   }
 }
 
@@ -217,8 +233,8 @@ template <int FMT>
 __global__ void k_tc_pack_exp(TcGeom t, const float2* __restrict__ A, const float* __restrict__ scale,
                               uint16_t* __restrict__ B) {
   const int g = blockIdx.y;
-  const size_t per = (size_t)t.nexp * t.Kx;
-  uint16_t* Bg = B + (size_t)g * per;
+  const int nimg = tc_images(FMT);
+  uint16_t* Bg = B + (size_t)g * tc_exp_group_elems(t, FMT);
   const float inv = scale[g] > 0.f ? 1.0f / scale[g] : 0.f;
   const int keep = t.keep[g];
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < t.nexp * t.Kx; idx += gridDim.x * blockDim.x) {
@@ -233,8 +249,12 @@ __global__ void k_tc_pack_exp(TcGeom t, const float2* __restrict__ A, const floa
       v = (c == 0) ? (cp == 0 ? re : im) : (cp == 0 ? -im : re);
     }
     // N tiles of 256 rows are stored one after another, each its own image
+    // (BF16: the tile's head image, then its remainder image)
     const int tile = nr >> 8, rr = nr & 255;
-    Bg[(size_t)tile * 256 * t.Kx + core_off(rr, kk, t.Kx)] = (uint16_t)(pack2<FMT>(v, 0.f) & 0xFFFF);
+    uint16_t* Bt = Bg + (size_t)tile * nimg * 256 * t.Kx;
+    const uint32_t p = pack2<FMT>(v, 0.f);
+    Bt[core_off(rr, kk, t.Kx)] = (uint16_t)(p & 0xFFFF);
+    if (nimg == 2) Bt[256 * t.Kx + core_off(rr, kk, t.Kx)] = (uint16_t)(pack2<FMT>(v - unpack2<FMT>(p).x, 0.f) & 0xFFFF);
   }
 }
 
@@ -246,13 +266,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
                                                               const uint16_t* __restrict__ Bpk,
                                                               float2* __restrict__ out, int n_lines,
                                                               int* status) {
+  // BF16 splits the FP32 source into head + remainder (16-bit sources are FP16 only)
+  static_assert(FMT == 0 || SRC_BYTES == 4, "the BF16 compression takes FP32 sources");
+  constexpr int NI = tc_images(FMT);
   extern __shared__ __align__(1024) unsigned char tsm[];
   const int g = blockIdx.y;
   const int l0 = blockIdx.x * t.lt;
   unsigned char* stg = tsm;                                   // staging [lt][ncc][n_occ][box0]
-  uint16_t* At = (uint16_t*)(tsm + t.stg_bytes);              // 128 x Kc core image
-  uint16_t* Bt = At + 128 * t.Kc;                             // npad x Kc core image
-  uint64_t* bars = (uint64_t*)(Bt + (size_t)t.npad * t.Kc);   // [0] load, [1] mma
+  uint16_t* At = (uint16_t*)(tsm + t.stg_bytes);              // 128 x Kc core image (head)
+  uint16_t* Al = At + (NI - 1) * 128 * t.Kc;                  // 128 x Kc remainder (BF16)
+  uint16_t* Bt = Al + 128 * t.Kc;                             // npad x Kc core image(s) of A_g
+  uint64_t* bars = (uint64_t*)(Bt + (size_t)NI * t.npad * t.Kc);  // [0] load, [1] mma
   uint32_t* tmem_slot = (uint32_t*)(bars + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
@@ -268,7 +292,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
   const uint32_t idesc = idesc_f16(FMT, t.npad);
   const int x0 = ((2 * g * t.w) / t.xalign) * t.xalign;
   const int shift = 2 * g * t.w - x0;
-  const uint32_t bbytes = (uint32_t)(t.npad * t.Kc * 2);
+  const uint32_t bbytes = (uint32_t)(NI * t.npad * t.Kc * 2);
   uint32_t ph_ld = 0, ph_mma = 0;
   bool ok = true;
   uint64_t* stuck = nullptr;
@@ -278,7 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
     if (tid == 0) {
       mbar_expect_tx(&bars[0], (uint32_t)t.stg_tx + bbytes);
       tma_load_4d(stg, &tmap, x0, 0, c * t.ncc, l0, &bars[0]);
-      bulk_g2s(Bt, Bpk + ((size_t)g * t.nchunks + c) * t.npad * t.Kc, bbytes, &bars[0]);
+      bulk_g2s(Bt, Bpk + ((size_t)g * t.nchunks + c) * NI * t.npad * t.Kc, bbytes, &bars[0]);
     }
     if (!(ok = block_wait(&bars[0], ph_ld))) {
       stuck = &bars[0];
@@ -288,19 +312,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
     for (int nl = 0; nl < t.ncc; ++nl) {
       const size_t base = ((size_t)(l * t.ncc + nl) * t.n_occ + q) * t.box0 + shift;
       for (int tau = 0; tau < t.w; ++tau) {
-        uint32_t pk;
+        uint32_t pk, pl = 0u;
         if (SRC_BYTES == 4) {
           const float* s = (const float*)stg + base + 2 * tau;
           pk = pack2<FMT>(s[0], s[1]);
+          if (NI == 2) {
+            const float2 h = unpack2<FMT>(pk);
+            pl = pack2<FMT>(s[0] - h.x, s[1] - h.y);
+          }
         } else {
           const uint16_t* s = (const uint16_t*)stg + base + 2 * tau;
           pk = (uint32_t)s[0] | ((uint32_t)s[1] << 16);
         }
         const int k = 2 * (nl * t.w + tau);
         *(uint32_t*)(At + core_off(m, k, t.Kc)) = pk;
+        if (NI == 2) *(uint32_t*)(Al + core_off(m, k, t.Kc)) = pl;
       }
     }
-    for (int k = 2 * t.ncc * t.w; k < t.Kc; k += 2) *(uint32_t*)(At + core_off(m, k, t.Kc)) = 0u;
+    for (int k = 2 * t.ncc * t.w; k < t.Kc; k += 2) {
+      *(uint32_t*)(At + core_off(m, k, t.Kc)) = 0u;
+      if (NI == 2) *(uint32_t*)(Al + core_off(m, k, t.Kc)) = 0u;
+    }
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -311,6 +343,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
         const uint64_t ad = umma_desc(At + ks * 16 * 8, 128, sbo);
         const uint64_t bd = umma_desc(Bt + ks * 16 * 8, 128, sbo);
         mma_f16(tmem, ad, bd, idesc, (c > 0 || ks > 0) ? 1u : 0u);
+        if (NI == 2) {
+          // remainder x head and head x remainder into the same accumulator
+          mma_f16(tmem, umma_desc(Al + ks * 16 * 8, 128, sbo), bd, idesc, 1u);
+          mma_f16(tmem, ad, umma_desc(Bt + (size_t)t.npad * t.Kc + ks * 16 * 8, 128, sbo), idesc, 1u);
+        }
       }
       mma_commit(&bars[1]);
     }
@@ -357,13 +394,14 @@ template <int FMT>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const float2* __restrict__ H,
                                                             const uint16_t* __restrict__ Bpk,
                                                             float2* __restrict__ V, int n_rows, int* status) {
+  constexpr int NI = tc_images(FMT);
   extern __shared__ __align__(1024) unsigned char tsm[];
   const int g = blockIdx.y;
   const int r0 = blockIdx.x * t.lt;
   uint16_t* Ah = (uint16_t*)tsm;                        // 128 x Kx head
   uint16_t* Al = Ah + 128 * t.Kx;                       // 128 x Kx remainder
-  uint16_t* Bt = Al + 128 * t.Kx;                       // 256 x Kx
-  uint64_t* bars = (uint64_t*)(Bt + 256 * t.Kx);
+  uint16_t* Bt = Al + 128 * t.Kx;                       // 256 x Kx head (+ 256 x Kx remainder, BF16)
+  uint64_t* bars = (uint64_t*)(Bt + NI * 256 * t.Kx);
   uint32_t* tmem_slot = (uint32_t*)(bars + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
@@ -400,8 +438,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
     const int nrows = min(256, t.nexp - nt * 256);  // multiple of 16
     const uint32_t bbytes = (uint32_t)(nrows * t.Kx * 2);
     if (tid == 0) {
-      mbar_expect_tx(&bars[0], bbytes);
-      bulk_g2s(Bt, Bpk + (size_t)g * t.nexp * t.Kx + (size_t)nt * 256 * t.Kx, bbytes, &bars[0]);
+      const uint16_t* src = Bpk + (size_t)g * tc_exp_group_elems(t, FMT) + (size_t)nt * NI * 256 * t.Kx;
+      mbar_expect_tx(&bars[0], NI * bbytes);
+      bulk_g2s(Bt, src, bbytes, &bars[0]);
+      if (NI == 2) bulk_g2s(Bt + 256 * t.Kx, src + 256 * t.Kx, bbytes, &bars[0]);
     }
     if (!(ok = block_wait(&bars[0], ph_ld))) {
       stuck = &bars[0];
@@ -415,6 +455,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
         const uint64_t bd = umma_desc(Bt + ks * 16 * 8, 128, sbo);
         mma_f16(tmem, umma_desc(Ah + ks * 16 * 8, 128, sbo), bd, idesc, ks > 0 ? 1u : 0u);
         mma_f16(tmem, umma_desc(Al + ks * 16 * 8, 128, sbo), bd, idesc, 1u);
+        if (NI == 2)  // head of H x remainder of A_g
+          mma_f16(tmem, umma_desc(Ah + ks * 16 * 8, 128, sbo),
+                  umma_desc(Bt + 256 * t.Kx + ks * 16 * 8, 128, sbo), idesc, 1u);
       }
       mma_commit(&bars[1]);
     }
@@ -491,10 +534,17 @@ bool make_tc_tmap(const TcGeom& t, const void* base, int lines, int ebytes, CUte
   return r == CUDA_SUCCESS;
 }
 
-size_t tc_compress_smem(const TcGeom& t) {
-  return (size_t)t.stg_bytes + (size_t)128 * t.Kc * 2 + (size_t)t.npad * t.Kc * 2 + 64;
+size_t tc_compress_smem(const TcGeom& t, int fmt) {
+  const int ni = tc_images(fmt);
+  return (size_t)t.stg_bytes + (size_t)ni * 128 * t.Kc * 2 + (size_t)ni * t.npad * t.Kc * 2 + 64;
 }
-size_t tc_expand_smem(const TcGeom& t) { return (size_t)2 * 128 * t.Kx * 2 + (size_t)256 * t.Kx * 2 + 64; }
+size_t tc_expand_smem(const TcGeom& t, int fmt) {
+  return (size_t)2 * 128 * t.Kx * 2 + (size_t)tc_images(fmt) * 256 * t.Kx * 2 + 64;
+}
+size_t tc_pack_comp_elems(const TcGeom& t, int fmt) {
+  return (size_t)t.G * t.nchunks * t.npad * t.Kc * tc_images(fmt);
+}
+size_t tc_pack_exp_elems(const TcGeom& t, int fmt) { return (size_t)t.G * tc_exp_group_elems(t, fmt); }
 
 cudaError_t launch_tc_pack(const TcGeom& t, int fmt, const float2* A, const float* scale, uint16_t* Bc,
                            uint16_t* Bx, cudaStream_t st) {
@@ -512,7 +562,7 @@ cudaError_t launch_tc_pack(const TcGeom& t, int fmt, const float2* A, const floa
 template <int FMT, int SB>
 static cudaError_t launch_comp_t(const CUtensorMap& map, const TcGeom& t, const uint16_t* Bc, float2* out,
                                  int lines, int* status, cudaStream_t st) {
-  const size_t sm = tc_compress_smem(t);
+  const size_t sm = tc_compress_smem(t, FMT);
   static size_t attr = 0;
   if (sm > attr) {
     cudaFuncSetAttribute(k_tc_compress<FMT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -526,7 +576,6 @@ static cudaError_t launch_comp_t(const CUtensorMap& map, const TcGeom& t, const 
 cudaError_t launch_tc_compress(const CUtensorMap& map, const TcGeom& t, int fmt, int src_bytes, const uint16_t* Bc,
                                float2* out, int lines, int* status, cudaStream_t st) {
   if (fmt == 1 && src_bytes == 4) return launch_comp_t<1, 4>(map, t, Bc, out, lines, status, st);
-  if (fmt == 1 && src_bytes == 2) return launch_comp_t<1, 2>(map, t, Bc, out, lines, status, st);
   if (fmt == 0 && src_bytes == 4) return launch_comp_t<0, 4>(map, t, Bc, out, lines, status, st);
   if (fmt == 0 && src_bytes == 2) return launch_comp_t<0, 2>(map, t, Bc, out, lines, status, st);
   return cudaErrorInvalidValue;
@@ -535,7 +584,7 @@ cudaError_t launch_tc_compress(const CUtensorMap& map, const TcGeom& t, int fmt,
 template <int FMT>
 static cudaError_t launch_exp_t(const TcGeom& t, const float2* H, const uint16_t* Bx, float2* V, int rows,
                                 int* status, cudaStream_t st) {
-  const size_t sm = tc_expand_smem(t);
+  const size_t sm = tc_expand_smem(t, FMT);
   static size_t attr = 0;
   if (sm > attr) {
     cudaFuncSetAttribute(k_tc_expand<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

@@ -66,10 +66,10 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_grad(const float2* __restrict
 // ------------------------------------------------------------------ host side --
 // (left out when the kernel above is compiled for a host emulation)
 #ifndef GPJC_DEVICE_SOURCE_ONLY
-cudaError_t launch_tv_grad(const float2* u, float2* g, int nz, int ny, int nx, float eps, cudaStream_t st) {
+cudaError_t launch_tv_grad(const float2* u, float2* g, int nz, int ny, int nx, float eps2, cudaStream_t st) {
   const size_t total = (size_t)nz * ny * nx;
   const int blocks = (int)std::min<size_t>((total + kTvThreads - 1) / kTvThreads, (size_t)152 * 8);
-  note_launches(1); k_tv_grad<<<blocks, kTvThreads, 0, st>>>(u, g, nz, ny, nx, eps * eps);
+  note_launches(1); k_tv_grad<<<blocks, kTvThreads, 0, st>>>(u, g, nz, ny, nx, eps2);
   return cudaGetLastError();
 }
 #endif  // GPJC_DEVICE_SOURCE_ONLY

@@ -99,6 +99,9 @@ _sig("gpjc_simulate", [_P, _P, _P, _P])
 _sig("gpjc_simulate_adjoint", [_P, _P, _P, _P])
 _sig("gpjc_recon", [_P, _P, _P, C.POINTER(ReconParams), C.POINTER(ReconInfo), _P])
 _sig("gpjc_apply_EH_static", [_P, _P, _P, _P, _P])
+_sig("gpjc_query", [_P, C.c_int32, C.c_int32, _I32P, C.POINTER(C.c_uint64)])
+_sig("gpjc_debug_fail_allocations", [C.c_int64], None)
+_sig("gpjc_probe_fp32_tflops", [C.c_int32, C.POINTER(C.c_double)])
 _sig("gpjc_batch_create", [C.c_int32, C.POINTER(_P), C.c_int32, C.POINTER(_P)])
 _sig("gpjc_batch_destroy", [_P], None)
 _sig("gpjc_recon_batched", [_P, C.POINTER(_P), C.POINTER(_P), C.c_int32, _I32P, _P])
@@ -109,6 +112,19 @@ _sig("gpjc_batch_info", [_P, _I32P, C.POINTER(C.c_int64)])
 def check(status: int) -> None:
     if status != GPJC_OK:
         raise GpjcError(status, _lib.gpjc_last_error().decode())
+
+
+def probe_fp32_tflops(iters: int = 200000) -> float:
+    """Measured FP32 FMA throughput (TFLOP/s) of the current device."""
+    v = C.c_double(0.0)
+    check(_lib.gpjc_probe_fp32_tflops(int(iters), C.byref(v)))
+    return float(v.value)
+
+
+def debug_fail_allocations(n: int) -> None:
+    """Test hook: the library's (n+1)-th and later device allocations fail
+    with GPJC_ENOMEM; n < 0 restores normal allocation."""
+    _lib.gpjc_debug_fail_allocations(int(n))
 
 
 def lib():
@@ -131,6 +147,8 @@ def tv_grad(x: torch.Tensor, eps: float, out: Optional[torch.Tensor] = None, str
     nz, ny, nx = x.shape
     if out is None:
         out = torch.empty_like(x)
+    if out.shape != x.shape or out.device != x.device:
+        raise ValueError(f"out must have the shape {tuple(x.shape)} and device of x")
     check(_lib.gpjc_tv_grad(_dptr(x, torch.complex64), nz, ny, nx, float(eps), _dptr(out, torch.complex64),
                             _stream(stream)))
     return out
@@ -274,6 +292,13 @@ class Groups:
             o += int(k) * ns
         return out, (ritz if info.block > 0 else None)
 
+    def query(self, precision: int = FP32, nchunk: int = 0):
+        """(N'_tx, device bytes an Operator(self, ..., precision, nchunk) allocates)."""
+        ntxc = C.c_int32(0)
+        nbytes = C.c_uint64(0)
+        check(_lib.gpjc_query(self.h, precision, nchunk, C.byref(ntxc), C.byref(nbytes)))
+        return int(ntxc.value), int(nbytes.value)
+
     def gram(self) -> np.ndarray:
         g = self.plan.geom
         ns = g.nc * g.w
@@ -393,8 +418,17 @@ def apply_EH_static(groups: Groups, coil: torch.Tensor, y: torch.Tensor, out=Non
     g = groups.plan.geom
     if out is None:
         out = torch.empty((g.nz, g.ny, g.nx), dtype=torch.complex64, device=y.device)
-    check(_lib.gpjc_apply_EH_static(groups.h, _dptr(coil, torch.complex64), _dptr(y, torch.complex64),
-                                    _dptr(out, torch.complex64), _stream(stream)))
+    if tuple(coil.shape) != (g.nc, g.nz, g.ny, g.nx):
+        raise ValueError(f"coil must have shape {(g.nc, g.nz, g.ny, g.nx)}, got {tuple(coil.shape)}")
+    if tuple(y.shape) != (g.n_lines, groups.plan.ntx_c):
+        raise ValueError(f"y must have shape {(g.n_lines, groups.plan.ntx_c)}, got {tuple(y.shape)}")
+    if tuple(out.shape) != (g.nz, g.ny, g.nx):
+        raise ValueError(f"out must have shape {(g.nz, g.ny, g.nx)}, got {tuple(out.shape)}")
+    if not (y.device == coil.device == out.device) or y.device.type != "cuda":
+        raise ValueError("coil, y and out must be on one CUDA device")
+    with torch.cuda.device(y.device):
+        check(_lib.gpjc_apply_EH_static(groups.h, _dptr(coil, torch.complex64), _dptr(y, torch.complex64),
+                                        _dptr(out, torch.complex64), _stream(stream)))
     return out
 
 

@@ -3,7 +3,8 @@
 Tolerances: the FP32 path must reproduce the oracle's images within
 NRMSE 1e-5 (range-normalised, Sec. 3.4); single operator applications are
 held to a relative L2 error of 1e-5 (FP32 rounding over a few FFT stages and
-a length-N_s contraction stays well below that).  Integer bookkeeping is
+a length-N_s contraction stays well below that).  Every such check also
+bounds the largest element error (tests/_checks.py).  Integer bookkeeping is
 compared bit for bit.
 """
 import math
@@ -12,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from _checks import check_close, check_image
 from paper_2601_05418_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -40,8 +42,6 @@ def to_np(t):
     return t.detach().cpu().numpy().astype(np.complex128)
 
 
-def rel(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
 def ragged_geometry():
@@ -130,10 +130,10 @@ def test_simulate_matches_oracle(gp, name):
     op = gp.Operator(gp.Groups.from_matrices(plan, A), to_dev(coils))
     S = to_np(op.simulate(to_dev(x)))
     S_ref = O.E_apply(g, coils, x)
-    assert rel(S, S_ref) < 1e-5
+    check_close(S, S_ref, 1e-5)
     y = synth.complex_normal(S_ref.shape, 6)
     xa = to_np(op.simulate_adjoint(to_dev(y)))
-    assert rel(xa, O.EH_apply(g, coils, y)) < 1e-5
+    check_close(xa, O.EH_apply(g, coils, y), 1e-5)
 
 
 @pytest.mark.parametrize("name", ["2d128", "ragged", "3d56"])
@@ -146,10 +146,10 @@ def test_compressed_operator_matches_oracle(gp, name):
     x = synth.complex_normal(g.shape, 8)
     y = to_np(op.E(to_dev(x)))
     y_ref = O.Ec_apply(g, coils, As, x)
-    assert rel(y, y_ref) < 1e-5
+    check_close(y, y_ref, 1e-5)
     v = synth.complex_normal(y_ref.shape, 9)
     xa = to_np(op.EH(to_dev(v)))
-    assert rel(xa, O.EcH_apply(g, coils, As, v)) < 1e-5
+    check_close(xa, O.EcH_apply(g, coils, As, v), 1e-5)
     # adjoint identity of the GPU pair itself
     lhs = np.vdot(y, v)
     rhs = np.vdot(x, xa)
@@ -157,7 +157,7 @@ def test_compressed_operator_matches_oracle(gp, name):
     # normal operator and ||E_c x||^2
     qq = torch.zeros(1, dtype=torch.float64, device=DEV)
     n = to_np(op.normal(to_dev(x), qq=qq))
-    assert rel(n, O.EcH_apply(g, coils, As, y_ref)) < 1e-5
+    check_close(n, O.EcH_apply(g, coils, As, y_ref), 1e-5)
     assert abs(qq.item() - np.vdot(y_ref, y_ref).real) < 1e-5 * np.vdot(y_ref, y_ref).real
 
 
@@ -169,7 +169,7 @@ def test_coil_chunking_is_exact(gp, nchunk):
     plan = gp.Plan(g)
     op = gp.Operator(gp.Groups.from_matrices(plan, As), to_dev(coils), nchunk=nchunk)
     x = synth.complex_normal(g.shape, 11)
-    assert rel(to_np(op.E(to_dev(x))), O.Ec_apply(g, coils, As, x)) < 1e-5
+    check_close(to_np(op.E(to_dev(x))), O.Ec_apply(g, coils, As, x), 1e-5)
 
 
 def test_keep_all_is_lossless(gp):
@@ -193,7 +193,7 @@ def test_compress_matches_oracle(gp, name):
     plan = gp.Plan(g)
     grp = gp.Groups.from_matrices(plan, As)
     Sc = to_np(gp.compress(grp, to_dev(S)))
-    assert rel(Sc, O.compress(g, As, S)) < 1e-5
+    check_close(Sc, O.compress(g, As, S), 1e-5)
 
 
 # ------------------------------------------------------------ groups --
@@ -269,7 +269,7 @@ def test_cg_matches_oracle_same_matrices(gp, name):
     op = gp.Operator(gp.Groups.from_matrices(gp.Plan(g), As), to_dev(coils))
     x, info = op.recon(to_dev(Sc), alg=gp.CG, iters=20, history=True)
     assert info["status"] == 0
-    assert O.nrmse(to_np(x), x_ref) < 1e-5
+    check_image(to_np(x), x_ref, 1e-5)
     pb = O.Problem(g, coils, As)
     _, hist = O.cg(None, pb.EcH(Sc), 20, fwd=pb.Ec, adj=pb.EcH)
     np.testing.assert_allclose(info["history"][:len(hist)], hist, rtol=1e-3)
@@ -289,8 +289,7 @@ def test_cg_end_to_end_2d128(gp):
     Sc_d = gp.compress(grp, to_dev(S))
     op = gp.Operator(grp, c_d)
     x, info = op.recon(Sc_d, alg=gp.CG, iters=wl.iters)
-    err = O.nrmse(to_np(x), x_ref)
-    assert err < 1e-5, err
+    check_image(to_np(x), x_ref, 1e-5)
 
 
 def test_cg_warm_start_and_zero_iterations(gp):
@@ -304,7 +303,7 @@ def test_cg_warm_start_and_zero_iterations(gp):
     xs = synth.complex_normal(g.shape, 24) * 0.1
     ref, _ = O.cg(pb.normal_c, pb.EcH(Sc), 6, x0=xs, fwd=pb.Ec, adj=pb.EcH)
     x, _ = op.recon(to_dev(Sc), alg=gp.CG, iters=6, x0=to_dev(xs))
-    assert O.nrmse(to_np(x), ref) < 1e-5
+    check_image(to_np(x), ref, 1e-5)
 
 
 def test_fista_matches_oracle_small(gp):
@@ -322,7 +321,7 @@ def test_fista_matches_oracle_small(gp):
     _, info = op.recon(to_dev(Sc), alg=gp.FISTA, iters=1, lam=1e-3, haar_levels=3, power_iters=20)
     assert abs(info["lipschitz"] - L) < 1e-5 * L
     x, info = op.recon(to_dev(Sc), alg=gp.FISTA, iters=30, lam=1e-3, lipschitz=L, haar_levels=3)
-    assert O.nrmse(to_np(x), x_ref) < 1e-5
+    check_image(to_np(x), x_ref, 1e-5)
 
 
 def test_graph_and_eager_agree(gp):
@@ -348,7 +347,7 @@ def test_3d_cg_end_to_end(gp):
     grp = gp.Groups.build(plan, c_d, to_dev(case.roi, np.uint8))
     op = gp.Operator(grp, c_d)
     x, _ = op.recon(gp.compress(grp, to_dev(S)), alg=gp.CG, iters=wl.iters)
-    assert O.nrmse(to_np(x), x_ref) < 1e-5
+    check_image(to_np(x), x_ref, 1e-5)
 
 
 # ------------------------------------------------------------ FFT lengths --
@@ -366,7 +365,7 @@ def test_two_pass_fft_lengths_match_oracle(gp, n):
     As, _, _ = O.build_groups(g, coils, roi)
     plan = gp.Plan(g)
     op = gp.Operator(gp.Groups.from_matrices(plan, As), to_dev(coils))
-    assert rel(to_np(op.simulate(to_dev(x))), O.E_apply(g, coils, x)) < 1e-5
-    assert rel(to_np(op.E(to_dev(x))), O.Ec_apply(g, coils, As, x)) < 1e-5
+    check_close(to_np(op.simulate(to_dev(x))), O.E_apply(g, coils, x), 1e-5)
+    check_close(to_np(op.E(to_dev(x))), O.Ec_apply(g, coils, As, x), 1e-5)
     v = synth.complex_normal((g.n_lines, plan.ntx_c), 32)
-    assert rel(to_np(op.EH(to_dev(v))), O.EcH_apply(g, coils, As, v)) < 1e-5
+    check_close(to_np(op.EH(to_dev(v))), O.EcH_apply(g, coils, As, v), 1e-5)

@@ -1,20 +1,23 @@
 """Tensor-core (tcgen05) compression and operator: BF16 / FP16 operands,
 FP32 accumulation, against the FP64 oracle.
 
-Tolerances: a 16-bit operand carries a relative rounding error of 2^-9
-(BF16) or 2^-12 (FP16); a contraction over N_s terms with random phases
-keeps the relative error of each output at that order, so single
-applications are held to a relative L2 error of 1e-2 (BF16) / 2e-3 (FP16).
-Images: the compressed hybrid data entering A_g^H are split into two 16-bit
-parts (no rounding there), so the remaining image error comes from rounding
-A_g, the readout spectra and the raw data once each.  With FP16 that stays
-below the NRMSE 1e-3 bar; with BF16 (8x coarser) the measured error of the
-same reconstructions is 1e-3 to 3e-3, held here to 5e-3.
+Tolerances.  FP16 rounds each operand once (relative error 2^-12); a
+contraction over N_s terms with random phases keeps the relative error of
+each output at that order, so single FP16 applications are held to a
+relative L2 error of 2e-3.  BF16 carries every operand as a head and a
+remainder (both BF16, three MMAs per K step), so each product keeps about
+2 x 8 mantissa bits (relative error ~2^-16 plus the dropped
+remainder x remainder term, ~2^-18): single BF16 applications are held to
+1e-4.  Images: the compressed hybrid data entering A_g^H are always split
+into two 16-bit parts; both formats are held to the NRMSE 1e-3 bar of the
+16-bit path against the FP64 oracle.  Every check also bounds the largest
+element error (tests/_checks.py).
 """
 import numpy as np
 import pytest
 
 import oracle as O
+from _checks import check_close, check_image
 from paper_2601_05418_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -40,12 +43,10 @@ def to_np(t):
     return t.detach().cpu().numpy().astype(np.complex128)
 
 
-def rel(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
-TOL = {1: 1e-2, 2: 2e-3}  # BF16, FP16: single applications
-IMG = {1: 5e-3, 2: 1e-3}  # BF16, FP16: reconstructed images
+TOL = {1: 1e-4, 2: 2e-3}  # BF16 (split), FP16: single applications
+IMG = {1: 1e-3, 2: 1e-3}  # BF16, FP16: reconstructed images
 
 
 def geoms():
@@ -68,7 +69,7 @@ def test_tc_compress_matches_oracle(gp, name, prec):
     S = synth.complex_normal((g.n_lines, g.nc, g.ntx), 42)
     grp = gp.Groups.from_matrices(gp.Plan(g), As)
     Sc = to_np(gp.compress(grp, to_dev(S), prec))
-    assert rel(Sc, O.compress(g, As, S)) < TOL[prec]
+    check_close(Sc, O.compress(g, As, S), TOL[prec])
 
 
 @pytest.mark.parametrize("prec", [1, 2])
@@ -81,10 +82,10 @@ def test_tc_operator_matches_oracle(gp, name, prec):
     x = synth.complex_normal(g.shape, 44)
     y = to_np(op.E(to_dev(x)))
     y_ref = O.Ec_apply(g, coils, As, x)
-    assert rel(y, y_ref) < TOL[prec]
+    check_close(y, y_ref, TOL[prec])
     v = synth.complex_normal(y_ref.shape, 45)
     xa = to_np(op.EH(to_dev(v)))
-    assert rel(xa, O.EcH_apply(g, coils, As, v)) < TOL[prec]
+    check_close(xa, O.EcH_apply(g, coils, As, v), TOL[prec])
 
 
 def test_tc_unsupported_group_map_is_rejected(gp):
@@ -112,8 +113,8 @@ def test_tc_cg_image_within_1e3(gp, prec):
     op = gp.Operator(grp, c_d, prec)
     x, info = op.recon(gp.compress(grp, to_dev(S), prec), alg=gp.CG, iters=wl.iters)
     assert info["status"] == 0
-    err = O.nrmse(to_np(x), x_ref)
-    assert err < IMG[prec], err
+    e, m = check_image(to_np(x), x_ref, IMG[prec])
+    print(f"precision {prec}: NRMSE {e:.3e}, max element error {m:.3e}")
 
 
 @pytest.mark.parametrize("prec", [1, 2])
@@ -130,8 +131,8 @@ def test_tc_fista_image_within_1e3(gp, prec):
     op = gp.Operator(gp.Groups.from_matrices(gp.Plan(g), As), to_dev(coils), prec)
     x, _ = op.recon(gp.compress(op.groups, to_dev(S), prec), alg=gp.FISTA, iters=30, lam=1e-3, lipschitz=L,
                     haar_levels=3)
-    err = O.nrmse(to_np(x), x_ref)
-    assert err < IMG[prec], err
+    e, m = check_image(to_np(x), x_ref, IMG[prec])
+    print(f"precision {prec}: NRMSE {e:.3e}, max element error {m:.3e}")
 
 
 @pytest.mark.parametrize("prec", [0, 2, 1])
@@ -154,10 +155,9 @@ def test_fista_2d256_full_size_vs_stored_oracle(gp, prec):
     x, info = op.recon(Sc, alg=gp.FISTA, iters=wl.iters, lam=wl.lam, lipschitz=float(ref["L"]),
                        haar_levels=wl.haar_levels)
     assert info["status"] == 0
-    err = O.nrmse(to_np(x), ref["x"])
-    bound = {0: 1e-5, 2: 1e-3, 1: 5e-3}[prec]
-    print(f"2d256 FISTA precision {prec}: NRMSE vs oracle {err:.3e}")
-    assert err < bound, err
+    bound = {0: 1e-5, 2: 1e-3, 1: 1e-3}[prec]
+    e, m = check_image(to_np(x), ref["x"], bound)
+    print(f"2d256 FISTA precision {prec}: NRMSE vs oracle {e:.3e}, max element error {m:.3e}")
 
 
 @pytest.mark.parametrize("prec", [1, 2])
@@ -183,4 +183,4 @@ def test_tc_adjoint_row_pieces_bit_exact(gp, name, pieces, prec, monkeypatch):
     xn = opn.EH(v)
     torch.cuda.synchronize()
     assert torch.equal(x1, xn)
-    assert rel(to_np(xn), O.EcH_apply(g, coils, As, v.cpu().numpy().astype(np.complex128))) < TOL[prec]
+    check_close(to_np(xn), O.EcH_apply(g, coils, As, v.cpu().numpy().astype(np.complex128)), TOL[prec])
