@@ -567,6 +567,21 @@ def _blas_threads():
         return os.cpu_count() or 1
 
 
+def _one_thread_pair_s(workload):
+    """One oracle pair timed in a child process whose BLAS / OpenMP pools
+    are limited to one thread (numpy's FFT is single-threaded anyway)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1")
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; from paper_2601_05418_gb300 import synth; "
+            "pb, Sc, _, _ = bench._oracle_problem(synth.workload(%r)); bench._oracle_pairs(pb, Sc, 1); "
+            "print(json.dumps(bench._oracle_pairs(pb, Sc, 1)[0]))") % (ROOT, workload)
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+        return float(r.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None
+
+
 def _oracle_pairs(pb, Sc, n):
     """Times n oracle E_c + E_c^H pairs (FP64, numpy); returns seconds each."""
     x = pb.EcH(Sc)
@@ -586,14 +601,7 @@ def cpu_baseline(wl, n_pairs=8):
     pb, Sc, t_group, t_comp = _oracle_problem(wl)
     _oracle_pairs(pb, Sc, 1)
     ts = _oracle_pairs(pb, Sc, n_pairs)
-    t1 = None
-    try:
-        from threadpoolctl import threadpool_limits
-
-        with threadpool_limits(limits=1):
-            t1 = _oracle_pairs(pb, Sc, 1)[0]
-    except Exception:
-        pass
+    t1 = _one_thread_pair_s(wl.name)
     pair_s = statistics.median(ts)
     return {"value": round(1.0 / pair_s, 4), "unit": "pairs/s", "cores": _blas_threads(), "kind": "oracle",
             "sample": f"{n_pairs} FP64 oracle E_c + E_c^H pairs of one {wl.name} slice (median), after one "
@@ -620,14 +628,7 @@ def run_reference(args, rank, world):
     t0 = time.perf_counter()
     ts = _oracle_pairs(pb, Sc, args.steps)
     wall = time.perf_counter() - t0
-    t1 = None
-    try:
-        from threadpoolctl import threadpool_limits
-
-        with threadpool_limits(limits=1):
-            t1 = _oracle_pairs(pb, Sc, 1)[0]
-    except Exception:
-        pass
+    t1 = _one_thread_pair_s(wl.name)
     total = sum(ts)
     value = args.steps / total
     import oracle as O

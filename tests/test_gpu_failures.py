@@ -53,8 +53,10 @@ def test_nan_in_data_reports_nonfinite_and_device_stays_usable(gp, alg):
     bad[g.n_lines // 2, 3] = np.nan  # planted on the host
     a = gp.CG if alg == "cg" else gp.FISTA
     kw = {} if alg == "cg" else {"lam": 1e-3, "haar_levels": 2}
-    _, info = op.recon(to_dev(bad), alg=a, iters=5, **kw)
-    assert info["status"] == gp.GPJC_ENONFINITE
+    # gpjc_recon returns the device-side verdict as its status
+    with pytest.raises(gp.GpjcError) as ei:
+        op.recon(to_dev(bad), alg=a, iters=5, **kw)
+    assert ei.value.status == gp.GPJC_ENONFINITE
     # the same operator and device still reconstruct the clean data correctly
     x, info = op.recon(to_dev(Sc), alg=gp.CG, iters=10)
     assert info["status"] == 0
