@@ -274,6 +274,8 @@ typedef struct gpjc_recon_params {
   int32_t haar_levels;  /* FISTA: Haar levels J (nx, ny divisible by 2^J, J <= 5)   */
   int32_t use_x0;       /* nonzero: d_x holds the starting image                     */
   int32_t use_graph;    /* nonzero: capture the iteration loop in a CUDA graph      */
+  double lambda_tv;     /* FISTA: weight of the smoothed isotropic TV (Eq. 17), 0 = off */
+  double tv_eps;        /* FISTA: TV smoothing eps (> 0, eps^2 a normal FP32 number)     */
 } gpjc_recon_params;
 
 typedef struct gpjc_recon_info {
@@ -283,9 +285,16 @@ typedef struct gpjc_recon_info {
 } gpjc_recon_info;
 
 /* Compressed reconstruction of d_Sc [n_lines][ntx_c] into d_x [nz][ny][nx]
- * (CG-SENSE or FISTA l1-Haar).  The loop runs on the device without host
- * synchronisation; the call synchronises `stream` once at the end when
- * `info` is non-NULL (to report status, L and history). */
+ * (Sec. 3.4): CG-SENSE (CGNR on E_c^H E_c x = E_c^H S', Eq. 16's least
+ * squares) or FISTA for 1/2 ||E_c x - S'||^2 + lambda ||W x||_1 (orthonormal
+ * Haar detail bands) + lambda_tv TV_eps(x) (Eq. 17, TV by its smooth
+ * approximation in the gradient step; gpjc_tv_grad's definition).  With
+ * lipschitz <= 0 the step size comes from power iteration of E_c^H E_c, plus
+ * 8 lambda_tv / tv_eps (the TV gradient's Lipschitz bound); a given
+ * lipschitz must bound the whole gradient.  The loop runs on the device
+ * without host synchronisation; the call synchronises `stream` once at the
+ * end when `info` is non-NULL (to report status, L and history), and then
+ * returns GPJC_ENONFINITE when a non-finite step scalar appeared. */
 gpjc_status gpjc_recon(const gpjc_op* op, const float* d_Sc, float* d_x, const gpjc_recon_params* params,
                        gpjc_recon_info* info, void* stream);
 

@@ -1267,16 +1267,20 @@ static gpjc_status recon_body(gpjc_op* op, const float2* Sc, float2* x, const gp
       CK(launch_sum_parts(op->xparts, op->nchunk_a, L, op->vtmp, op->partials, op->counter, sc + SC_NV, st));
       CK(launch_scale_by(op->vv, op->vtmp, sc + SC_NV, L, sc + SC_LIP, st));
     }
+    // the smoothed TV gradient is Lipschitz with constant ||D||^2 / eps <= 8 / eps
+    if (rp.lambda_tv > 0.0) CK(launch_add_scalar(sc + SC_LIP, 8.0 * rp.lambda_tv / rp.tv_eps, st));
   }
   if (!rp.use_x0) CK(launch_zero(x, L, st));
   CK(launch_copy(op->vy, x, L, st));
+  const bool tv = rp.lambda_tv > 0.0;
   double t = 1.0;
   for (int it = 0; it < rp.iters; ++it) {
     if ((s = op_normal_parts(op, op->vy, nullptr, st))) return s;
+    if (tv) CK(launch_tv_grad(op->vy, op->vtmp, g.nz, g.ny, g.nx, (float)(rp.tv_eps * rp.tv_eps), st));
     const double tn = 0.5 * (1.0 + std::sqrt(1.0 + 4.0 * t * t));
     const double ck = (t - 1.0) / tn;
     CK(launch_fista_step(g, op->xparts, op->nchunk_a, x, op->vy, op->vb, sc + SC_LIP, rp.lambda, rp.haar_levels, ck,
-                         op->status, st));
+                         tv ? op->vtmp : nullptr, rp.lambda_tv, op->status, st));
     t = tn;
   }
   return GPJC_OK;
@@ -1296,6 +1300,13 @@ extern "C" gpjc_status gpjc_recon(const gpjc_op* cop, const float* d_Sc, float* 
     if (g.nx % ts || g.ny % ts) return fail(GPJC_EINVAL, "nx, ny must be divisible by 2^haar_levels");
     if (!(rp.lambda >= 0.0) || !std::isfinite(rp.lambda)) return fail(GPJC_EINVAL, "lambda must be finite and >= 0");
     if (!std::isfinite(rp.lipschitz)) return fail(GPJC_EINVAL, "lipschitz must be finite");
+    if (!(rp.lambda_tv >= 0.0) || !std::isfinite(rp.lambda_tv))
+      return fail(GPJC_EINVAL, "lambda_tv must be finite and >= 0");
+    if (rp.lambda_tv > 0.0) {
+      const double e2 = rp.tv_eps * rp.tv_eps;
+      if (!(rp.tv_eps > 0.0) || !(e2 >= (double)FLT_MIN) || !(e2 <= (double)FLT_MAX))
+        return fail(GPJC_EINVAL, "tv_eps must be > 0 with tv_eps^2 a normal FP32 number");
+    }
   }
   cudaStream_t st = (cudaStream_t)stream;
   gpjc_status s;

@@ -130,9 +130,11 @@ cudaError_t launch_axpby(float2* y, const float2* a, const float2* b, float alph
                          cudaStream_t st);
 cudaError_t launch_scale_by(float2* v, const float2* src, const double* nrm2, size_t L, double* Lout,
                             cudaStream_t st);
+// tvg: smoothed-TV gradient of y (nullptr: no TV term), weighted by lam_tv
 cudaError_t launch_fista_step(const Geo& g, const float2* parts, int nchunk, float2* x, float2* y,
                               const float2* b, const double* Lip, double lam, int levels, double ck,
-                              int* status, cudaStream_t st);
+                              const float2* tvg, double lam_tv, int* status, cudaStream_t st);
+cudaError_t launch_add_scalar(double* d, double v, cudaStream_t st);
 cudaError_t launch_copy(float2* dst, const float2* src, size_t n, cudaStream_t st);
 cudaError_t launch_zero(float2* dst, size_t n, cudaStream_t st);
 cudaError_t launch_set_scalar(double* d, double v, cudaStream_t st);

@@ -164,7 +164,8 @@ cudaError_t launch_zero(float2* dst, size_t n, cudaStream_t st) {
 
 // ------------------------------------------------------------------ FISTA --
 // One block per 2^J x 2^J tile (J <= 5).  Per element:
-//   z  = y - (N y - b) / L
+//   z  = y - (N y - b + lam_tv grad TV_eps(y)) / L   (TV term of Eq. 17 when
+//        lam_tv > 0; its gradient is computed beforehand by k_tv_grad)
 //   x' = W^H soft_{lam/L}(W z)       (details only; tile-local Haar)
 //   y' = x' + ck (x' - x),  x <- x'
 __device__ __forceinline__ void haar_level_fwd(float2* t, float2* tmp, int ts, int h) {
@@ -208,7 +209,8 @@ __device__ __forceinline__ void haar_level_inv(float2* t, float2* tmp, int ts, i
 __global__ void __launch_bounds__(256) k_fista_step(Geo g, const float2* __restrict__ parts, int nchunk,
                                                     float2* __restrict__ x, float2* __restrict__ y,
                                                     const float2* __restrict__ bvec, const double* Lip,
-                                                    float lam, int levels, float ck, int* status) {
+                                                    float lam, int levels, float ck,
+                                                    const float2* __restrict__ tvg, float lam_tv, int* status) {
   __shared__ float2 t[32 * 33];
   __shared__ float2 tmp[32 * 33];
   const int ts = 1 << levels;
@@ -228,7 +230,14 @@ __global__ void __launch_bounds__(256) k_fista_step(Geo g, const float2* __restr
     float2 ny_ = parts[idx];
     for (int ch = 1; ch < nchunk; ++ch) ny_ = cadd(ny_, parts[ch * L + idx]);
     const float2 yv = y[idx], bv = bvec[idx];
-    t[r * 33 + c] = make_float2(yv.x - (ny_.x - bv.x) * invL, yv.y - (ny_.y - bv.y) * invL);
+    // gradient of the data term, plus lam_tv times the smoothed-TV gradient of y
+    float2 gr = make_float2(ny_.x - bv.x, ny_.y - bv.y);
+    if (tvg) {
+      const float2 tv = tvg[idx];
+      gr.x = fmaf(lam_tv, tv.x, gr.x);
+      gr.y = fmaf(lam_tv, tv.y, gr.y);
+    }
+    t[r * 33 + c] = make_float2(yv.x - gr.x * invL, yv.y - gr.y * invL);
   }
   __syncthreads();
   for (int lev = 0, h = ts; lev < levels; ++lev, h >>= 1) haar_level_fwd(t, tmp, 33, h);
@@ -254,10 +263,17 @@ __global__ void __launch_bounds__(256) k_fista_step(Geo g, const float2* __restr
 
 cudaError_t launch_fista_step(const Geo& g, const float2* parts, int nchunk, float2* x, float2* y,
                               const float2* b, const double* Lip, double lam, int levels, double ck,
-                              int* status, cudaStream_t st) {
+                              const float2* tvg, double lam_tv, int* status, cudaStream_t st) {
   const int ts = 1 << levels;
   const int ntiles = (g.nx / ts) * (g.ny / ts) * g.nz;
-  note_launches(1); k_fista_step<<<ntiles, 256, 0, st>>>(g, parts, nchunk, x, y, b, Lip, (float)lam, levels, (float)ck, status);
+  note_launches(1); k_fista_step<<<ntiles, 256, 0, st>>>(g, parts, nchunk, x, y, b, Lip, (float)lam, levels, (float)ck,
+                                                          tvg, (float)lam_tv, status);
+  return cudaGetLastError();
+}
+
+__global__ void k_add_scalar(double* d, double v) { d[0] += v; }
+cudaError_t launch_add_scalar(double* d, double v, cudaStream_t st) {
+  note_launches(1); k_add_scalar<<<1, 1, 0, st>>>(d, v);
   return cudaGetLastError();
 }
 

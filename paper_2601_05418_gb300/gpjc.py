@@ -53,7 +53,7 @@ class GroupsInfo(C.Structure):
 class ReconParams(C.Structure):
     _fields_ = [("alg", C.c_int32), ("iters", C.c_int32), ("lambda_", C.c_double), ("lipschitz", C.c_double),
                 ("power_iters", C.c_int32), ("haar_levels", C.c_int32), ("use_x0", C.c_int32),
-                ("use_graph", C.c_int32)]
+                ("use_graph", C.c_int32), ("lambda_tv", C.c_double), ("tv_eps", C.c_double)]
 
 
 class ReconInfo(C.Structure):
@@ -396,15 +396,17 @@ class Operator:
 
     def recon(self, Sc: torch.Tensor, alg: int = CG, iters: int = 20, lam: float = 0.0, lipschitz: float = 0.0,
               power_iters: int = 20, haar_levels: int = 4, x0: Optional[torch.Tensor] = None,
-              use_graph: bool = True, history: bool = False, sync: bool = True, out=None, stream=None):
-        """Returns (x, info dict).  With sync=False nothing is read back."""
+              use_graph: bool = True, history: bool = False, sync: bool = True, out=None, stream=None,
+              lam_tv: float = 0.0, tv_eps: float = 1e-3):
+        """Returns (x, info dict).  With sync=False nothing is read back.
+        FISTA: lam weights the Haar l1 term, lam_tv the smoothed TV term."""
         if out is None:
             out = (x0.clone() if x0 is not None else
                    torch.empty(self.image_shape, dtype=torch.complex64, device=Sc.device))
         elif x0 is not None:
             out.copy_(x0)
         rp = ReconParams(alg, iters, float(lam), float(lipschitz), power_iters, haar_levels,
-                         1 if x0 is not None else 0, 1 if use_graph else 0)
+                         1 if x0 is not None else 0, 1 if use_graph else 0, float(lam_tv), float(tv_eps))
         hist = np.zeros(iters + 1, np.float64) if history else None
         info = ReconInfo(0, 0.0, hist.ctypes.data_as(C.POINTER(C.c_double)) if hist is not None else None)
         check(_lib.gpjc_recon(self.h, _dptr(Sc, torch.complex64), _dptr(out, torch.complex64), C.byref(rp),
