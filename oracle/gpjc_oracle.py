@@ -421,6 +421,32 @@ def decoupled_ls(geom, coils, As, Sc) -> np.ndarray:
     return rho.reshape(nz, ny, nx)
 
 
+def decoupled_cg(geom, coils, As, Sc, iters: int) -> np.ndarray:
+    """Algorithm #1 (Sec. 3.4) with an iterative solver per readout
+    subproblem, the form the paper runs (LSQR per aliased set): steps 1 and
+    3 as in `decoupled_ls`; in step 2 every aliased set Y solves its own
+    normal equations N_Y rho_Y = b_Y by CG with its own scalars, exactly
+    `iters` iterations (stopping early only when ||r_Y||^2 == 0; CG on the
+    normal equations has LSQR's iterates in exact arithmetic)."""
+    nx, ny, nz = geom.nx, geom.ny, geom.nz
+    sets, F, U = aliased_sets(geom)
+    ht = F.conj().T @ Sc  # step 1
+    Gs = [readout_Ec_row(geom, coils, As, r % ny, r // ny) for r in range(ny * nz)]
+    rho = np.zeros((ny * nz, nx), np.complex128)
+    for Y in sets:  # step 2: the set's own normal equations and CG
+        m = len(Y)
+        N = np.zeros((m * nx, m * nx), np.complex128)
+        b = np.zeros(m * nx, np.complex128)
+        for a, ra in enumerate(Y):
+            b[a * nx:(a + 1) * nx] = Gs[ra].conj().T @ ht[ra]
+            for c, rb in enumerate(Y):
+                N[a * nx:(a + 1) * nx, c * nx:(c + 1) * nx] = Gs[ra].conj().T @ (U[ra, rb] * Gs[rb])
+        sol, _ = cg(lambda v: N @ v, b, iters)
+        for a, ra in enumerate(Y):  # step 3
+            rho[ra] = sol[a * nx:(a + 1) * nx]
+    return rho.reshape(nz, ny, nx)
+
+
 def dense_Ec(geom, coils, As) -> np.ndarray:
     """E' = A E (Eq. 14) as a dense matrix (tiny grids only)."""
     E = dense_E(geom, coils)

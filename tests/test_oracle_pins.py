@@ -362,6 +362,38 @@ def test_decoupled_ls_3d_caipi_is_the_global_least_squares():
     assert np.linalg.norm(x_dec - x_ls) < 1e-8 * np.linalg.norm(x_ls)
 
 
+def test_decoupled_cg_converges_to_decoupled_ls():
+    """Per-set CG (algorithm #1 with an iterative subproblem solver) reaches
+    the exact per-set least squares of `decoupled_ls` once the iterations
+    reach the set's unknown count (2 rows x 8 pixels = 16)."""
+    g, c = _tiny2d(nx=8, ny=12, nc=3, os=2, cycles=2.0, kappa_y=1.3, n_groups=2, keep=5,
+                   lines="regular", r=2)
+    As, _, _ = O.build_groups(g, c, np.ones(g.shape, np.uint8))
+    Sc = O.compress(g, As, O.E_apply(g, c, _rand(g.shape, 66))) + 0.05 * _rand((g.n_lines, O.ntx_compressed(g.patch_group, g.keep)), 67)
+    x_ls = O.decoupled_ls(g, c, As, Sc)
+    x_cg = O.decoupled_cg(g, c, As, Sc, 16)
+    assert np.linalg.norm(x_cg - x_ls) < 1e-8 * np.linalg.norm(x_ls)
+    # fewer iterations than unknowns: not yet there (the test would pass
+    # trivially if the iteration count were ignored)
+    assert np.linalg.norm(O.decoupled_cg(g, c, As, Sc, 3) - x_ls) > 1e-4 * np.linalg.norm(x_ls)
+
+
+def test_decoupled_cg_with_one_set_is_global_cg():
+    """A mask whose samples form no lattice (R = 5 on 12 rows) couples all
+    rows into one aliased set: per-set CG is then the global CG of
+    Eq. 16 (same recurrences, same iterates)."""
+    g, c = _tiny2d(nx=8, ny=12, nc=3, os=2, cycles=2.0, kappa_y=1.3, n_groups=2, keep=4,
+                   lines="regular", r=5)
+    sets, _, _ = O.aliased_sets(g)
+    assert len(sets) == 1
+    As, _, _ = O.build_groups(g, c, np.ones(g.shape, np.uint8))
+    Sc = O.compress(g, As, O.E_apply(g, c, _rand(g.shape, 68)))
+    pb = O.Problem(g, c, As)
+    x_glob, _ = O.cg(pb.normal_c, pb.EcH(Sc), 7)
+    x_dec = O.decoupled_cg(g, c, As, Sc, 7)
+    assert np.linalg.norm(x_dec - x_glob) < 1e-10 * np.linalg.norm(x_glob)
+
+
 def test_cg_reaches_least_squares():
     g, c = _tiny2d(nx=4, ny=4, nc=2, os=2, cycles=2.0, n_groups=2, keep=3)
     roi = np.ones(g.shape, np.uint8)
