@@ -99,6 +99,14 @@ gpjc_status gpjc_plan_create(const gpjc_geom* geom, gpjc_plan** out);
 void gpjc_plan_destroy(gpjc_plan* plan);
 /* Compressed readout length N'_tx (Eq. 15). */
 gpjc_status gpjc_plan_ntx_c(const gpjc_plan* plan, int32_t* ntx_c);
+/* Aliased sets of the phase-encode mask (Sec. 3.4: the pixel sets that
+ * alias together, which decouple the least-squares problem): the connected
+ * components of the nonzero pattern of F^H M^T M F (|entry| > 1e-9 of the
+ * largest), with F the centred unitary phase-encode DFT and M the sampled
+ * lines.  h_set_of_row [ny nz] (raster z, y; may be NULL) receives each
+ * row's set, the sets numbered in the order of their first row; *n_sets
+ * (may be NULL) their number.  Computed on the host at plan creation. */
+gpjc_status gpjc_plan_sets(const gpjc_plan* plan, int32_t* h_set_of_row, int32_t* n_sets);
 /* Host copies of the bookkeeping: any pointer may be NULL.
  * h_off [ntx/w], h_ref [n_groups] (first patch of each group),
  * h_line_of [nz*ny] (line index of (kz, ky) or -1). */
@@ -263,7 +271,12 @@ gpjc_status gpjc_simulate(const gpjc_op* op, const float* d_x, float* d_S, void*
 gpjc_status gpjc_simulate_adjoint(const gpjc_op* op, const float* d_S, float* d_x, void* stream);
 
 /* ------------------------------------------------------------------ recon -- */
-typedef enum gpjc_alg { GPJC_CG = 0, GPJC_FISTA = 1 } gpjc_alg;
+/* GPJC_DECOUPLED: the hybrid-space reconstruction (Sec. 3.4, algorithm #1,
+ * Eq. 16): the least-squares problem decouples over the aliased sets of
+ * the phase-encode mask (gpjc_plan_sets); every set runs its own CG (own
+ * alpha, beta, stopping when its ||r||^2 == 0) on its readout subproblem.
+ * The history holds the sum over the sets of ||r||^2. */
+typedef enum gpjc_alg { GPJC_CG = 0, GPJC_FISTA = 1, GPJC_DECOUPLED = 2 } gpjc_alg;
 
 typedef struct gpjc_recon_params {
   int32_t alg;          /* gpjc_alg                                                  */

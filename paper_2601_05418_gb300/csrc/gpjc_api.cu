@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <complex>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -160,8 +161,89 @@ struct gpjc_plan {
   RTiles rt_f, rt_a;  // register-tiled readout stage (rb == 0: use the per-output kernels)
   bool tc_ok;          // tensor-core compression available (periodic group map, sizes in range)
   TcGeom tc32, tc16;   // for FP32 sources (raw data) and 16-bit sources (hybrid data)
+  // aliased sets of the mask (hybrid-space reconstruction, Sec. 3.4): set of
+  // each phase-encode row (raster z, y), sets numbered by their first row;
+  // CSR member lists (rows ascending) on the host and the device
+  int n_sets;
+  std::vector<int> set_of_row, set_ptr, set_rows;
+  int *d_set_of_row, *d_set_ptr, *d_set_rows;
   DevMem mem;
 };
+
+// Aliased sets of a phase-encode mask: the connected components of the
+// nonzero pattern of U = F^H M^T M F (F the centred unitary phase-encode DFT,
+// M the line selection), |U| > 1e-9 max |U|.  U[r, r''] depends only on the
+// row difference: U = c(y - y'', z - z'') / (N_y N_z) with the mask's
+// autocorrelation c(dy, dz) = sum_lines exp(2 pi i (ky_c dy / N_y +
+// kz_c dz / N_z)), computed as a per-kz sum over the lines followed by a
+// DFT over kz.  The components of this circulant pattern are the cosets of
+// the subgroup of Z_Ny x Z_Nz that the nonzero differences generate: a
+// union-find pass over all rows is needed only for a difference not yet in
+// that subgroup (each such pass at least doubles it).
+static void aliased_sets(int ny, int nz, const std::vector<int>& ky, const std::vector<int>& kz, int* n_sets,
+                         std::vector<int>* set_of_row, std::vector<int>* set_ptr, std::vector<int>* set_rows) {
+  const int rows = ny * nz;
+  const int nl = (int)ky.size();
+  // A[kz][dy] = sum_{lines with this kz} exp(2 pi i ky_c dy / N_y)
+  std::vector<std::complex<double>> A((size_t)nz * ny, 0.0);
+  for (int l = 0; l < nl; ++l) {
+    const double kyc = (double)(ky[l] - ny / 2);
+    std::complex<double>* a = &A[(size_t)kz[l] * ny];
+    for (int dy = 0; dy < ny; ++dy) {
+      const double ph = 2.0 * M_PI * std::fmod(kyc * dy, (double)ny) / ny;
+      a[dy] += std::complex<double>(std::cos(ph), std::sin(ph));
+    }
+  }
+  // c(dy, dz) = sum_kz exp(2 pi i kz_c dz / N_z) A[kz][dy]
+  std::vector<double> mag((size_t)nz * ny, 0.0);
+  for (int dz = 0; dz < nz; ++dz)
+    for (int dy = 0; dy < ny; ++dy) {
+      std::complex<double> c = 0.0;
+      for (int k = 0; k < nz; ++k) {
+        const double ph = 2.0 * M_PI * std::fmod((double)(k - nz / 2) * dz, (double)nz) / nz;
+        c += std::complex<double>(std::cos(ph), std::sin(ph)) * A[(size_t)k * ny + dy];
+      }
+      mag[(size_t)dz * ny + dy] = std::abs(c);
+    }
+  const double thr = 1e-9 * mag[0];  // |c(0)| = number of lines = max |c|
+  std::vector<int> parent(rows);
+  for (int r = 0; r < rows; ++r) parent[r] = r;
+  auto find = [&](int a) {
+    while (parent[a] != a) {
+      parent[a] = parent[parent[a]];
+      a = parent[a];
+    }
+    return a;
+  };
+  for (int dz = 0; dz < nz; ++dz)
+    for (int dy = 0; dy < ny; ++dy) {
+      const int d = dz * ny + dy;
+      if (d == 0 || !(mag[d] > thr)) continue;
+      if (find(0) == find(d)) continue;  // already in the generated subgroup
+      for (int r = 0; r < rows; ++r) {
+        const int y = r % ny, z = r / ny;
+        const int q = ((z + dz) % nz) * ny + (y + dy) % ny;
+        const int a = find(r), b = find(q);
+        if (a != b) parent[std::max(a, b)] = std::min(a, b);
+      }
+    }
+  // number the sets by their first row
+  std::vector<int> id(rows, -1);
+  set_of_row->assign(rows, 0);
+  int ns = 0;
+  for (int r = 0; r < rows; ++r) {
+    const int root = find(r);
+    if (id[root] < 0) id[root] = ns++;
+    (*set_of_row)[r] = id[root];
+  }
+  set_ptr->assign(ns + 1, 0);
+  for (int r = 0; r < rows; ++r) ++(*set_ptr)[(*set_of_row)[r] + 1];
+  for (int k = 0; k < ns; ++k) (*set_ptr)[k + 1] += (*set_ptr)[k];
+  set_rows->assign(rows, 0);
+  std::vector<int> fill(set_ptr->begin(), set_ptr->end() - 1);
+  for (int r = 0; r < rows; ++r) (*set_rows)[fill[(*set_of_row)[r]]++] = r;
+  *n_sets = ns;
+}
 
 // Tensor-core compression geometry for sources of `ebytes` bytes per real
 // element; false when the group map or the sizes do not fit the kernels.
@@ -323,6 +405,10 @@ extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
   g.pg = d_pg; g.poff = d_poff; g.keep = d_keep; g.aoff = d_aoff; g.out_tbase = d_tb; g.out_abase = d_ab;
   g.out_astride = d_as; g.line_ky = d_ky; g.line_kz = d_kz; g.line_of = d_lof; g.ay = ay; g.az = az;
   g.tw_x = tw_x; g.tw_y = tw_y; g.tw_z = tw_z; g.pre = pre; g.post_y = post_y; g.post_z = post_z;
+  aliased_sets(ny, nz, p->line_ky, p->line_kz, &p->n_sets, &p->set_of_row, &p->set_ptr, &p->set_rows);
+  if ((s = m.upload(&p->d_set_of_row, p->set_of_row)) || (s = m.upload(&p->d_set_ptr, p->set_ptr)) ||
+      (s = m.upload(&p->d_set_rows, p->set_rows)))
+    return s;
   CK(launch_make_tables(g, tw_x, tw_y, tw_z, pre, ay, az, p->cycles, p->kappa_y, p->kappa_z, 0));
   CK(launch_make_post(g, post_y, post_z, p->cycles, p->kappa_y, p->kappa_z, 0));
   p->tc_ok = make_tc_geom(p, 4, &p->tc32) && make_tc_geom(p, 2, &p->tc16);
@@ -389,6 +475,13 @@ extern "C" void gpjc_plan_destroy(gpjc_plan* plan) { delete plan; }
 extern "C" gpjc_status gpjc_plan_ntx_c(const gpjc_plan* plan, int32_t* ntx_c) {
   if (!plan || !ntx_c) return fail(GPJC_EINVAL, "null argument");
   *ntx_c = plan->ntxc;
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_plan_sets(const gpjc_plan* plan, int32_t* h_set_of_row, int32_t* n_sets) {
+  if (!plan) return fail(GPJC_EINVAL, "null plan");
+  if (n_sets) *n_sets = plan->n_sets;
+  if (h_set_of_row) std::copy(plan->set_of_row.begin(), plan->set_of_row.end(), h_set_of_row);
   return GPJC_OK;
 }
 
@@ -793,6 +886,8 @@ struct gpjc_op {
   double* sc;
   double* hist;
   int hist_len;
+  double* ds_rowval;  // per-set CG: one FP64 sum per image row
+  double* ds_sc;      // per-set CG: ||r||^2 (two, ping-pong) and <p, N p> per aliased set
   int* status;
   DevMem mem;
   DevMem lazy;
@@ -898,7 +993,7 @@ static OpSizes op_sizes(const gpjc_plan* p, gpjc_precision prec, int nchunk) {
   z.spectra = prec != GPJC_FP32 ? (size_t)g.rows * g.nc * g.ntx : 0;
   const size_t c64 = z.HN * nmax + z.HN + z.L * (size_t)z.nchunk_a_max + 6 * z.L + (g.dim3d ? z.HN : 0) + z.spectra;
   z.bytes = sizeof(float2) * c64 + sizeof(double) * (z.npartials + SC_N + z.hist_len) + 4 * sizeof(unsigned) +
-            4 * sizeof(int);
+            4 * sizeof(int) + sizeof(double) * ((size_t)g.rows + 3 * (size_t)p->n_sets);
   return z;
 }
 
@@ -958,6 +1053,8 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   if (g.dim3d && (s = m.alloc(&op->T, HN))) return s;
   op->npartials = (int)z.npartials;
   op->hist_len = (int)z.hist_len;
+  if ((s = m.alloc(&op->ds_rowval, (size_t)g.rows)) || (s = m.alloc(&op->ds_sc, 3 * (size_t)p->n_sets)))
+    return s;
   if ((s = m.alloc(&op->partials, op->npartials)) || (s = m.alloc(&op->counter, 4)) ||
       (s = m.alloc(&op->sc, SC_N)) || (s = m.alloc(&op->hist, op->hist_len)) || (s = m.alloc(&op->status, 4)))
     return s;
@@ -1256,6 +1353,41 @@ static gpjc_status recon_body(gpjc_op* op, const float2* Sc, float2* x, const gp
     }
     return GPJC_OK;
   }
+  if (rp.alg == GPJC_DECOUPLED) {
+    // hybrid-space reconstruction (Sec. 3.4, algorithm #1): CG with the
+    // scalars of each aliased set (b = E_c^H S' is steps 1 and the first
+    // half of 2: the phase-encode adjoint gives h~, the readout adjoint G^H)
+    const gpjc_plan* pl = op->plan;
+    const int ns = pl->n_sets;
+    double* rowval = op->ds_rowval;
+    double* rrs[2] = {op->ds_sc, op->ds_sc + ns};
+    double* pap = op->ds_sc + 2 * ns;
+    if (rp.use_x0) {
+      if ((s = op_normal_parts(op, x, nullptr, st))) return s;
+      CK(launch_sum_parts(op->xparts, op->nchunk_a, L, op->vtmp, nullptr, nullptr, nullptr, st));
+      CK(launch_axpby(op->vr, op->vb, op->vtmp, 1.0f, -1.0f, L, st));
+    } else {
+      CK(launch_zero(x, L, st));
+      CK(launch_copy(op->vr, op->vb, L, st));
+    }
+    CK(launch_copy(op->vp, op->vr, L, st));
+    CK(launch_ds_rowdot(op->vr, 1, L, g.rows, g.nx, nullptr, nullptr, rowval, st));
+    CK(launch_ds_setsum(rowval, pl->d_set_ptr, pl->d_set_rows, ns, rrs[0], op->hist, st));
+    for (int it = 0; it < rp.iters; ++it) {
+      double* rr = rrs[it % 2];
+      double* rrn = rrs[(it + 1) % 2];
+      if ((s = op_normal_parts(op, op->vp, nullptr, st))) return s;
+      // q = N p (into vtmp) and <p, q> per set
+      CK(launch_ds_rowdot(op->xparts, op->nchunk_a, L, g.rows, g.nx, op->vtmp, op->vp, rowval, st));
+      CK(launch_ds_setsum(rowval, pl->d_set_ptr, pl->d_set_rows, ns, pap, nullptr, st));
+      CK(launch_ds_update1(g.rows, g.nx, pl->d_set_of_row, x, op->vr, op->vp, op->vtmp, rr, pap, rowval, op->status,
+                           st));
+      double* h = (it + 1 < op->hist_len) ? op->hist + it + 1 : nullptr;
+      CK(launch_ds_setsum(rowval, pl->d_set_ptr, pl->d_set_rows, ns, rrn, h, st));
+      CK(launch_ds_update2(g.rows, g.nx, pl->d_set_of_row, op->vp, op->vr, rr, rrn, st));
+    }
+    return GPJC_OK;
+  }
   // FISTA
   if (rp.lipschitz > 0.0) {
     CK(launch_set_scalar(sc + SC_LIP, rp.lipschitz, st));
@@ -1292,7 +1424,8 @@ extern "C" gpjc_status gpjc_recon(const gpjc_op* cop, const float* d_Sc, float* 
   gpjc_op* op = const_cast<gpjc_op*>(cop);
   const gpjc_recon_params rp = *params;
   const Geo& g = op->plan->geo;
-  if (rp.alg != GPJC_CG && rp.alg != GPJC_FISTA) return fail(GPJC_EINVAL, "unknown algorithm");
+  if (rp.alg != GPJC_CG && rp.alg != GPJC_FISTA && rp.alg != GPJC_DECOUPLED)
+    return fail(GPJC_EINVAL, "unknown algorithm");
   if (rp.iters < 0 || rp.iters > 100000) return fail(GPJC_EINVAL, "iters out of range");
   if (rp.alg == GPJC_FISTA) {
     if (rp.haar_levels < 0 || rp.haar_levels > 5) return fail(GPJC_EINVAL, "haar_levels must be in [0, 5]");

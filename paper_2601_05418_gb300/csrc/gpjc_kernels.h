@@ -135,6 +135,16 @@ cudaError_t launch_fista_step(const Geo& g, const float2* parts, int nchunk, flo
                               const float2* b, const double* Lip, double lam, int levels, double ck,
                               const float2* tvg, double lam_tv, int* status, cudaStream_t st);
 cudaError_t launch_add_scalar(double* d, double v, cudaStream_t st);
+// per-aliased-set CG (hybrid-space reconstruction): one block per image row
+cudaError_t launch_ds_rowdot(const float2* parts, int nchunk, size_t L, int rows, int nx, float2* out,
+                             const float2* a, double* rowval, cudaStream_t st);
+cudaError_t launch_ds_setsum(const double* rowval, const int* ptr, const int* rows, int n_sets, double* out,
+                             double* total, cudaStream_t st);
+cudaError_t launch_ds_update1(int rows, int nx, const int* set_of_row, float2* x, float2* r, const float2* p,
+                              const float2* q, const double* rr, const double* pap, double* rowval, int* status,
+                              cudaStream_t st);
+cudaError_t launch_ds_update2(int rows, int nx, const int* set_of_row, float2* p, const float2* r, const double* rr,
+                              const double* rr_new, cudaStream_t st);
 cudaError_t launch_copy(float2* dst, const float2* src, size_t n, cudaStream_t st);
 cudaError_t launch_zero(float2* dst, size_t n, cudaStream_t st);
 cudaError_t launch_set_scalar(double* d, double v, cudaStream_t st);

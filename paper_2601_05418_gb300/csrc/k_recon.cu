@@ -162,6 +162,128 @@ cudaError_t launch_zero(float2* dst, size_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ per-set CG --
+// Hybrid-space reconstruction (Sec. 3.4, algorithm #1): the normal
+// equations decouple over the aliased sets of the mask (the phase-encode
+// projection F^H M^T M F is block-diagonal over them), so each set runs its
+// own CG on its rows with its own scalars alpha_Y, beta_Y.  The normal
+// operator is applied to all rows at once (it does not couple the sets);
+// the scalars are FP64 sums over each set's rows: one block per row forms
+// the row's sum, and one block adds the rows of every set in the order of
+// its member list (deterministic).
+
+// v = sum_c parts[c] (row r, written to out when out != nullptr);
+// rowval[r] = Re <a_r, v_r>  (a == nullptr: ||v_r||^2)
+__global__ void __launch_bounds__(kVecThreads) k_ds_rowdot(const float2* __restrict__ parts, int nchunk, size_t L,
+                                                          int nx, float2* __restrict__ out,
+                                                          const float2* __restrict__ a, double* __restrict__ rowval) {
+  __shared__ double red[32];
+  const size_t base = (size_t)blockIdx.x * nx;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    float2 v = parts[base + i];
+    for (int c = 1; c < nchunk; ++c) v = cadd(v, parts[c * L + base + i]);
+    if (out) out[base + i] = v;
+    const float2 u = a ? a[base + i] : v;
+    acc += (double)u.x * v.x + (double)u.y * v.y;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) rowval[blockIdx.x] = acc;
+}
+
+// out[s] = sum of rowval over the rows of set s (member-list order);
+// total (optional) = sum over all sets
+__global__ void __launch_bounds__(kVecThreads) k_ds_setsum(const double* __restrict__ rowval, const int* __restrict__ ptr,
+                                                          const int* __restrict__ rows, int n_sets,
+                                                          double* __restrict__ out, double* total) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int s = threadIdx.x; s < n_sets; s += blockDim.x) {
+    double v = 0.0;
+    for (int i = ptr[s]; i < ptr[s + 1]; ++i) v += rowval[rows[i]];
+    out[s] = v;
+    acc += v;
+  }
+  acc = block_sum(acc, red);
+  if (total && threadIdx.x == 0) *total = acc;
+}
+
+// per row r of set s = set_of_row[r]: alpha = rr[s] / pap[s] (0 when
+// rr[s] == 0); x += alpha p; r -= alpha q; rowval[r] = ||r_r||^2
+__global__ void __launch_bounds__(kVecThreads) k_ds_update1(int nx, const int* __restrict__ set_of_row,
+                                                           float2* __restrict__ x, float2* __restrict__ r,
+                                                           const float2* __restrict__ p, const float2* __restrict__ q,
+                                                           const double* __restrict__ rr, const double* __restrict__ pap,
+                                                           double* __restrict__ rowval, int* status) {
+  __shared__ double red[32];
+  const int s = set_of_row[blockIdx.x];
+  const double rrv = rr[s];
+  double alpha = rrv == 0.0 ? 0.0 : rrv / pap[s];
+  if (!isfinite(alpha)) {
+    if (threadIdx.x == 0) atomicExch(status, (int)kDevNonFinite);
+    alpha = 0.0;
+  }
+  const float af = (float)alpha;
+  const size_t base = (size_t)blockIdx.x * nx;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const float2 pv = p[base + i], qv = q[base + i];
+    float2 xv = x[base + i], rv = r[base + i];
+    xv.x = fmaf(af, pv.x, xv.x);
+    xv.y = fmaf(af, pv.y, xv.y);
+    rv.x = fmaf(-af, qv.x, rv.x);
+    rv.y = fmaf(-af, qv.y, rv.y);
+    x[base + i] = xv;
+    r[base + i] = rv;
+    acc += (double)rv.x * rv.x + (double)rv.y * rv.y;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) rowval[blockIdx.x] = acc;
+}
+
+// per row: beta = rr_new[s] / rr[s] (0 when rr[s] == 0); p = r + beta p
+__global__ void __launch_bounds__(kVecThreads) k_ds_update2(int nx, const int* __restrict__ set_of_row,
+                                                           float2* __restrict__ p, const float2* __restrict__ r,
+                                                           const double* __restrict__ rr,
+                                                           const double* __restrict__ rr_new) {
+  const int s = set_of_row[blockIdx.x];
+  const double rrv = rr[s];
+  if (rrv == 0.0) return;  // converged set: p is not used again
+  double beta = rr_new[s] / rrv;
+  if (!isfinite(beta)) beta = 0.0;
+  const float bf = (float)beta;
+  const size_t base = (size_t)blockIdx.x * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    const float2 rv = r[base + i];
+    float2 pv = p[base + i];
+    pv.x = fmaf(bf, pv.x, rv.x);
+    pv.y = fmaf(bf, pv.y, rv.y);
+    p[base + i] = pv;
+  }
+}
+
+cudaError_t launch_ds_rowdot(const float2* parts, int nchunk, size_t L, int rows, int nx, float2* out,
+                             const float2* a, double* rowval, cudaStream_t st) {
+  note_launches(1); k_ds_rowdot<<<rows, kVecThreads, 0, st>>>(parts, nchunk, L, nx, out, a, rowval);
+  return cudaGetLastError();
+}
+cudaError_t launch_ds_setsum(const double* rowval, const int* ptr, const int* rows, int n_sets, double* out,
+                             double* total, cudaStream_t st) {
+  note_launches(1); k_ds_setsum<<<1, kVecThreads, 0, st>>>(rowval, ptr, rows, n_sets, out, total);
+  return cudaGetLastError();
+}
+cudaError_t launch_ds_update1(int rows, int nx, const int* set_of_row, float2* x, float2* r, const float2* p,
+                              const float2* q, const double* rr, const double* pap, double* rowval, int* status,
+                              cudaStream_t st) {
+  note_launches(1); k_ds_update1<<<rows, kVecThreads, 0, st>>>(nx, set_of_row, x, r, p, q, rr, pap, rowval, status);
+  return cudaGetLastError();
+}
+cudaError_t launch_ds_update2(int rows, int nx, const int* set_of_row, float2* p, const float2* r, const double* rr,
+                              const double* rr_new, cudaStream_t st) {
+  note_launches(1); k_ds_update2<<<rows, kVecThreads, 0, st>>>(nx, set_of_row, p, r, rr, rr_new);
+  return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ FISTA --
 // One block per 2^J x 2^J tile (J <= 5).  Per element:
 //   z  = y - (N y - b + lam_tv grad TV_eps(y)) / L   (TV term of Eq. 17 when

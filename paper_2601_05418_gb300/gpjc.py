@@ -23,7 +23,7 @@ _lib = C.CDLL(LIB_PATH)
 
 GPJC_OK, GPJC_EINVAL, GPJC_ENOMEM, GPJC_ECUDA, GPJC_ETIMEOUT, GPJC_ENONFINITE, GPJC_EUNSUPPORTED = range(7)
 FP32, BF16, FP16 = 0, 1, 2
-CG, FISTA = 0, 1
+CG, FISTA, DECOUPLED = 0, 1, 2
 _P = C.c_void_p
 _I32P = C.POINTER(C.c_int32)
 
@@ -74,6 +74,7 @@ _sig("gpjc_version", [], C.c_char_p)
 _sig("gpjc_plan_create", [C.POINTER(Geom), C.POINTER(_P)])
 _sig("gpjc_plan_destroy", [_P], None)
 _sig("gpjc_plan_ntx_c", [_P, _I32P])
+_sig("gpjc_plan_sets", [_P, _I32P, _I32P])
 _sig("gpjc_plan_tables", [_P, _I32P, _I32P, _I32P])
 _sig("gpjc_build_groups", [_P, _P, _P, _P, C.POINTER(BuildParams), _P, C.POINTER(_P)])
 _sig("gpjc_groups_rebuild", [_P, _P, _P, _P, _P])
@@ -220,6 +221,14 @@ class Plan:
         v = C.c_int32()
         check(_lib.gpjc_plan_ntx_c(self.h, C.byref(v)))
         return v.value
+
+    def sets(self):
+        """(number of aliased sets, set index of every phase-encode row [nz*ny])."""
+        g = self.geom
+        sor = np.zeros(g.nz * g.ny, np.int32)
+        n = C.c_int32()
+        check(_lib.gpjc_plan_sets(self.h, _iptr(sor), C.byref(n)))
+        return int(n.value), sor
 
     def tables(self):
         g = self.geom
