@@ -250,6 +250,30 @@ gpjc_status gpjc_probe_fp32_tflops(int32_t iters, double* tflops);
  * restores normal allocation.  Process-wide. */
 void gpjc_debug_fail_allocations(int64_t n);
 void gpjc_op_destroy(gpjc_op* op);
+/* Nonlinear local-B0 modulation (Sec. 2.1-2.2, Eq. 2-3; the paper's
+ * primary hardware case): the modulation phase
+ *   phi(t, r) = sum_l a_l(t) B_l(r)
+ * of local B0 coils depends on the readout position, so the readout is not
+ * a DFT.  The operator stores each phase-encode row's compressed readout
+ * encoding matrix (Eq. 14)
+ *   G_row[off_p + k][x] = sum_{n,tau} A_{g(p)}[k][n w + tau] c_n(r)
+ *                         exp(-i [2 pi t_c x_c / N_tx + phi(p w + tau, r)]) / sqrt(N_tx)
+ * ([ny nz][ntx_c][nx] complex64 in device memory, built here on the device)
+ * and applies it as a batched matrix-vector product, followed by the
+ * phase-encode DFT and line gather of gpjc_apply_E.  The plan's wave
+ * parameters are not used by this operator.
+ *   d_coil   [nc][nz][ny][nx] complex64, device (referenced, as gpjc_op_create)
+ *   d_fields [n_fields][nz][ny][nx] float32 (radians at unit drive), device;
+ *            read during this call only
+ *   h_amps   [n_fields][ntx] float64 drive a_l(t), host
+ * Creates an FP32 operator: gpjc_apply_E / gpjc_apply_EH / gpjc_apply_normal
+ * / gpjc_recon (all algorithms) use the stored matrices;
+ * gpjc_simulate(_adjoint) return GPJC_EUNSUPPORTED for it, and
+ * gpjc_op_autotune keeps its fixed split.  Allocates the gpjc_query
+ * workspace plus 8 ny nz ntx_c nx bytes; synchronous.  GPJC_EINVAL for
+ * null or non-finite inputs or n_fields outside [0, 64]. */
+gpjc_status gpjc_op_create_local_b0(const gpjc_groups* groups, const float* d_coil, int32_t n_fields,
+                                    const float* d_fields, const double* h_amps, gpjc_op** out);
 /* Times the readout-stage coil-chunk choices on `stream` and keeps the
  * fastest (synchronous): the adjoint's chunk count, then the forward's, and
  * for GPJC_BF16 / GPJC_FP16 operators the number of row pieces (1, 2, 4, 8)

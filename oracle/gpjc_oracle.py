@@ -723,6 +723,20 @@ def Ec_apply_phase(geom, coils, As, phi: np.ndarray, rho: np.ndarray) -> np.ndar
     return F @ H
 
 
+def dense_Ec_phase(geom, coils, As, phi: np.ndarray) -> np.ndarray:
+    """E' = A E (Eq. 14) for a general phase as a dense matrix (tiny grids
+    only): rows (line, off_p + k), columns raster (z, y, x)."""
+    E = dense_E_phase(geom, coils, phi)
+    nl, nc, ntx, w = geom.n_lines, geom.nc, geom.ntx, geom.w
+    E = E.reshape(nl, nc, ntx, -1)
+    off = patch_offsets(geom.patch_group, geom.keep)
+    out = np.zeros((nl, ntx_compressed(geom.patch_group, geom.keep), E.shape[-1]), np.complex128)
+    for p, g in enumerate(geom.patch_group):
+        blk = E[:, :, p * w:(p + 1) * w, :].reshape(nl, nc * w, -1)
+        out[:, off[p]:off[p] + int(geom.keep[g]), :] = np.einsum("ki,lir->lkr", As[g], blk)
+    return out.reshape(nl * ntx_compressed(geom.patch_group, geom.keep), -1)
+
+
 def gram_phase(geom, coils, roi_idx, g: int, phi: np.ndarray, T=None) -> np.ndarray:
     """P_g (Eq. 7-11) for a general phase: encoding vectors of the group's
     first patch, entry (n, tau) = c~_n(r) exp(-i [2 pi t_c x_c / N_tx +

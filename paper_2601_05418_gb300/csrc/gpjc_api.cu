@@ -900,6 +900,9 @@ struct gpjc_op {
   cudaStream_t cap_st;
   cudaEvent_t ev_in, ev_out;
   bool legacy_readout;  // use the per-output readout kernels (set by GPJC_LEGACY_READOUT=1)
+  // nonlinear local-B0 operator: stored compressed readout matrices
+  // [rows][ntx_c][nx] replace the FFT readout stage (nullptr: wave operator)
+  float2* lb0_G;
   // optional per-stage timing with events (GPJC_STAGE_*)
   bool prof_on;
   std::vector<cudaEvent_t> prof_pool;
@@ -1075,6 +1078,7 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   }
   op->gexec = nullptr;
   op->graph_kernels = 0;
+  op->lb0_G = nullptr;
   {
     const char* e = getenv("GPJC_LEGACY_READOUT");
     op->legacy_readout = e && e[0] == '1';
@@ -1086,6 +1090,44 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   CK(cudaStreamCreateWithFlags(&op->cap_st, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&op->ev_in, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&op->ev_out, cudaEventDisableTiming));
+  *out = guard.release();
+  return GPJC_OK;
+}
+
+// Nonlinear local-B0 operator (Sec. 2.1-2.2, Eq. 2-3, 14): an FP32 operator
+// whose readout stage applies stored compressed readout matrices built here
+// from A_g, the coil maps and the local-B0 phase sum_l a_l(t) B_l(r).
+extern "C" gpjc_status gpjc_op_create_local_b0(const gpjc_groups* gr, const float* d_coil, int32_t n_fields,
+                                               const float* d_fields, const double* h_amps, gpjc_op** out) {
+  if (!gr || !d_coil || !out || (n_fields > 0 && (!d_fields || !h_amps)))
+    return fail(GPJC_EINVAL, "null argument");
+  *out = nullptr;
+  if (n_fields < 0 || n_fields > 64) return fail(GPJC_EINVAL, "n_fields must be in [0, 64]");
+  const gpjc_plan* p = gr->plan;
+  const Geo& g = p->geo;
+  if (lb0_build_tile(g.ns) < 1) return fail(GPJC_EUNSUPPORTED, "N_s too large for the matrix build");
+  for (size_t i = 0; i < (size_t)n_fields * g.ntx; ++i)
+    if (!std::isfinite(h_amps[i])) return fail(GPJC_EINVAL, "amplitudes must be finite");
+  gpjc_op* op = nullptr;
+  gpjc_status s = gpjc_op_create(gr, d_coil, GPJC_FP32, 1, &op);
+  if (s) return s;
+  std::unique_ptr<gpjc_op, void (*)(gpjc_op*)> guard(op, gpjc_op_destroy);
+  op->nchunk = 1;
+  // adjoint: enough (column chunk, row) blocks for two per SM, at least 32
+  // columns per chunk
+  {
+    int n = 1;
+    while (g.rows * n < 2 * 152 && n * 2 <= op->nchunk_a_max && g.ntxc / (n * 2) >= 32) n *= 2;
+    op->nchunk_a = n;
+  }
+  std::vector<float> amps((size_t)std::max(n_fields, 1) * g.ntx, 0.f);
+  for (size_t i = 0; i < (size_t)n_fields * g.ntx; ++i) amps[i] = (float)h_amps[i];
+  float* d_amps = nullptr;
+  float2* G = nullptr;
+  if ((s = op->mem.upload(&d_amps, amps)) || (s = op->mem.alloc(&G, (size_t)g.rows * g.ntxc * g.nx))) return s;
+  CK(launch_lb0_build(g, n_fields, (const float2*)d_coil, d_fields, d_amps, gr->A, G, 0));
+  CK(cudaDeviceSynchronize());
+  op->lb0_G = G;
   *out = guard.release();
   return GPJC_OK;
 }
@@ -1108,6 +1150,7 @@ extern "C" void gpjc_op_destroy(gpjc_op* op) {
 // tiles; 16-bit hybrid data + tensor-core compression for BF16 / FP16)
 static cudaError_t readout_fwd(const gpjc_op* op, const float2* x, cudaStream_t st) {
   const gpjc_plan* p = op->plan;
+  if (op->lb0_G) return launch_lb0_fwd(p->geo, op->lb0_G, x, op->Hpart, st);
   if (op->prec != GPJC_FP32) {
     // BF16: FP32 spectra, split into head + remainder by the compression GEMM;
     // FP16: FP16 spectra, one rounding
@@ -1127,6 +1170,7 @@ static cudaError_t readout_fwd(const gpjc_op* op, const float2* x, cudaStream_t 
 // readout stage of E_c^H from op->H2 into op->xparts
 static cudaError_t readout_adj(const gpjc_op* op, cudaStream_t st) {
   const gpjc_plan* p = op->plan;
+  if (op->lb0_G) return launch_lb0_adj(p->geo, op->lb0_G, op->H2, op->xparts, op->nchunk_a, st);
   if (op->prec != GPJC_FP32) {
     const int fmt = op->prec == GPJC_BF16 ? 1 : 0;
     TcGeom t = p->tc16;
@@ -1229,6 +1273,7 @@ static gpjc_status ensure_sim_buffers(gpjc_op* op) {
 
 extern "C" gpjc_status gpjc_simulate(const gpjc_op* cop, const float* d_x, float* d_S, void* stream) {
   if (!cop || !d_x || !d_S) return fail(GPJC_EINVAL, "null argument");
+  if (cop->lb0_G) return fail(GPJC_EUNSUPPORTED, "the uncompressed model is the wave model's (local-B0 operator)");
   gpjc_op* op = const_cast<gpjc_op*>(cop);
   gpjc_status s = ensure_sim_buffers(op);
   if (s) return s;
@@ -1241,6 +1286,7 @@ extern "C" gpjc_status gpjc_simulate(const gpjc_op* cop, const float* d_x, float
 
 extern "C" gpjc_status gpjc_simulate_adjoint(const gpjc_op* cop, const float* d_S, float* d_x, void* stream) {
   if (!cop || !d_x || !d_S) return fail(GPJC_EINVAL, "null argument");
+  if (cop->lb0_G) return fail(GPJC_EUNSUPPORTED, "the uncompressed model is the wave model's (local-B0 operator)");
   gpjc_op* op = const_cast<gpjc_op*>(cop);
   gpjc_status s = ensure_sim_buffers(op);
   if (s) return s;
@@ -1276,6 +1322,10 @@ static gpjc_status time_normal(gpjc_op* op, cudaStream_t st, cudaEvent_t e0, cud
 
 extern "C" gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchunk_out) {
   if (!op) return fail(GPJC_EINVAL, "null operator");
+  if (op->lb0_G) {  // stored-matrix operator: one forward plane, fixed adjoint split
+    if (nchunk_out) *nchunk_out = op->nchunk;
+    return GPJC_OK;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));

@@ -114,6 +114,13 @@ cudaError_t launch_form_A(const Geo& g, int b, const double2* U, const float2* T
 cudaError_t launch_compress_fp32(const Geo& g, const float2* S, int n_lines_in, const float2* AT, float2* Sc,
                                  cudaStream_t st);
 
+// ---- nonlinear local-B0 operator: stored compressed readout matrices (k_lb0.cu)
+int lb0_build_tile(int ns);  // x tile of the build (0: N_s too large)
+cudaError_t launch_lb0_build(const Geo& g, int nfields, const float2* coil, const float* fields, const float* amps,
+                             const float2* A, float2* G, cudaStream_t st);
+cudaError_t launch_lb0_fwd(const Geo& g, const float2* G, const float2* x, float2* H, cudaStream_t st);
+cudaError_t launch_lb0_adj(const Geo& g, const float2* G, const float2* H2, float2* xpart, int nsplit, cudaStream_t st);
+
 // ---- FP32 FMA throughput probe (k_probe.cu): synchronous, on the default stream
 cudaError_t probe_fma_tflops(int iters, double* tflops);
 

@@ -103,6 +103,7 @@ _sig("gpjc_apply_EH_static", [_P, _P, _P, _P, _P])
 _sig("gpjc_query", [_P, C.c_int32, C.c_int32, _I32P, C.POINTER(C.c_uint64)])
 _sig("gpjc_debug_fail_allocations", [C.c_int64], None)
 _sig("gpjc_probe_fp32_tflops", [C.c_int32, C.POINTER(C.c_double)])
+_sig("gpjc_op_create_local_b0", [_P, _P, C.c_int32, _P, _P, C.POINTER(_P)])
 _sig("gpjc_batch_create", [C.c_int32, C.POINTER(_P), C.c_int32, C.POINTER(_P)])
 _sig("gpjc_batch_destroy", [_P], None)
 _sig("gpjc_recon_batched", [_P, C.POINTER(_P), C.POINTER(_P), C.c_int32, _I32P, _P])
@@ -340,6 +341,23 @@ class Operator:
         self.plan = groups.plan
         self.h = _P()
         check(_lib.gpjc_op_create(groups.h, _dptr(coil, torch.complex64), precision, nchunk, C.byref(self.h)))
+
+    @classmethod
+    def local_b0(cls, groups: Groups, coil: torch.Tensor, fields: torch.Tensor, amps: np.ndarray) -> "Operator":
+        """Nonlinear local-B0 operator: stored compressed readout matrices
+        built from A_g, coil maps, fields [n_fields][nz][ny][nx] (float32,
+        device) and drive amps [n_fields][ntx] (host)."""
+        op = cls.__new__(cls)
+        op.groups, op.coil, op.precision = groups, coil, FP32
+        op.plan = groups.plan
+        op.h = _P()
+        a = np.ascontiguousarray(np.asarray(amps, np.float64))
+        f = fields.contiguous()
+        if f.dtype != torch.float32 or f.device != coil.device:
+            raise ValueError("fields must be float32 on the coil maps' device")
+        check(_lib.gpjc_op_create_local_b0(groups.h, _dptr(coil, torch.complex64), int(a.shape[0]),
+                                           C.c_void_p(f.data_ptr()), a.ctypes.data_as(_P), C.byref(op.h)))
+        return op
 
     def __del__(self):
         if getattr(self, "h", None):

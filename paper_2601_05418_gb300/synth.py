@@ -320,13 +320,24 @@ def workload(name: str) -> Workload:
     if name == "3d56":  # reduced 3D case the oracle finishes in seconds
         return Workload(name, geom_3d(56, 56, 40, 8, 6, 11, 1.5, 1.125, 12, 20.0),
                         seed=5, alg="cg", iters=10)
+    # the 3D volume with per-period groups: 14 cycles over 1344 samples give
+    # an integer period of 96 samples, cut into 48 groups of w = 2
+    if name == "3d224r1":
+        return Workload(name, geom_3d(224, 224, 160, 32, 6, 14, 6.0, 4.5, 48, 20.0, grouping="periodic"),
+                        seed=5, alg="cg", iters=10)
+    if name == "3d56r1":  # its reduced case: 336 samples, 14 cycles -> period 24, 12 groups of w = 2
+        return Workload(name, geom_3d(56, 56, 40, 8, 6, 14, 1.5, 1.125, 12, 8.0, grouping="periodic"),
+                        seed=5, alg="cg", iters=10)
     raise KeyError(name)
 
 
 def geom_3d(nx, ny, nz, nc, os, cycles, ky_amp, kz_amp, n_groups, cf,
-            ry=3, rz=3) -> Geometry:
+            ry=3, rz=3, grouping="contiguous") -> Geometry:
     ntx = os * nx
-    w, pg = grouping_contiguous(ntx, n_groups)
+    if grouping == "periodic":
+        w, pg = grouping_periodic(ntx, cycles, n_groups)
+    else:
+        w, pg = grouping_contiguous(ntx, n_groups)
     ky, kz = lines_caipi(ny, nz, ry, rz)
     return Geometry(nx=nx, ny=ny, nz=nz, nc=nc, os=os, cycles=float(cycles),
                     kappa_y=float(ky_amp), kappa_z=float(kz_amp), w=w,

@@ -616,6 +616,19 @@ def test_general_phase_reduces_to_the_wave():
     x = _rand(g.shape, 101)
     ref = O.Ec_apply(g, c, As, x)
     assert np.linalg.norm(O.Ec_apply_phase(g, c, As, phi, x) - ref) < 1e-12 * np.linalg.norm(ref)
+    # the dense compressed matrix of the general phase is the same model
+    D = O.dense_Ec_phase(g, c, As, phi)
+    assert np.linalg.norm(D @ x.ravel() - ref.ravel()) < 1e-12 * np.linalg.norm(ref)
+
+
+def test_dense_compressed_general_phase_reduces_to_the_wave():
+    """With the wave phase written as a general phase, dense_Ec_phase is the
+    wave model's dense_Ec."""
+    g, c = _tiny2d(nx=8, ny=6, nc=2, os=2, cycles=2.0, kappa_y=1.3, n_groups=2, keep=3, lines="regular", r=2)
+    As, _, _ = O.build_groups(g, c, np.ones(g.shape, np.uint8))
+    D1 = O.dense_Ec_phase(g, c, As, _wave_as_field(g))
+    D0 = O.dense_Ec(g, c, As)
+    assert np.linalg.norm(D1 - D0) < 1e-12 * np.linalg.norm(D0)
 
 
 def test_nonlinear_local_b0_model_equals_dense_E():
