@@ -432,7 +432,8 @@ def run_gpjc(args, rank, world, local):
     if wl.name == "2d256" and world == 1 and not args.no_extras:
         del op, grp
         torch.cuda.empty_cache()
-        out["workloads"] = {"3d224": run_3d(args, dev), "batch64": run_batch(args, 0, 1, local, emit=False)}
+        out["workloads"] = {"3d": run_3d(args, dev), "local_b0_2d256": run_local_b0(args, dev),
+                            "batch64": run_batch(args, 0, 1, local, emit=False)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl)
     if rank == 0:
@@ -452,72 +453,133 @@ def config_of(wl, ntx_c, pairs_per_step, power_iters, world):
 
 
 def run_3d(args, dev):
-    """The 3D volume (224 x 224 x 160, 32 coils, corkscrew wave, 48
-    contiguous groups compressed 20x, 3x3 CAIPI): group build + compression
-    timed once after one warm-up, then the CG-SENSE 10 reconstruction loop
-    (s/volume) timed over 3 runs after 3 warm-up runs, FP32 and BF16
-    operators on the same compressed data (BF16 compression for the BF16
-    operator).  Inputs resident in HBM; the 2.1 GB coil maps exceed L2."""
+    """The 3D volume (224 x 224 x 160, 32 coils, corkscrew wave, 6x
+    oversampling, 3x3 CAIPI) in two groupings: 48 contiguous readout
+    subregions compressed 20x (11 cycles, no integer period), and 48
+    per-period groups of w = 2 (14 cycles, period 96).  For each: group build
+    + compression timed once after one warm-up, then the CG-SENSE 10
+    reconstruction loop (s/volume) timed over 3 runs after 3 warm-up runs,
+    FP32 and BF16 operators (BF16 compression for the BF16 operator).  Inputs
+    resident in HBM; the 2.1 GB coil maps exceed L2."""
     import numpy as np
     import torch
 
     from paper_2601_05418_gb300 import gpjc, synth
 
-    wl = synth.workload("3d224")
-    g = wl.geom
-    rho = synth.phantom(g.nx, g.ny, g.nz)
-    roi = torch.from_numpy(synth.roi_mask(rho)).to(dev)
-    coils = torch.from_numpy(synth.coil_maps(g.nx, g.ny, g.nz, g.nc, wl.seed).astype(np.complex64)).to(dev)
-    rho_d = torch.from_numpy(rho.astype(np.complex64)).to(dev)
-    plan = gpjc.Plan(g)
-    stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    grp = gpjc.Groups.build(plan, coils, roi)
-    op = gpjc.Operator(grp, coils)
-    S = op.simulate(rho_d)
-    gen = torch.Generator(device=dev).manual_seed(wl.seed)
-    S += wl.sigma / np.sqrt(2) * torch.complex(torch.randn(S.shape, generator=gen, device=dev),
-                                               torch.randn(S.shape, generator=gen, device=dev))
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
-    res = {"config": {"workload": "3d224", "matrix": [g.nz, g.ny, g.nx], "coils": g.nc, "os": g.os,
-                      "groups": g.n_groups, "w": g.w, "keep": int(g.keep[0]), "ntx_c": int(plan.ntx_c),
-                      "n_lines": g.n_lines, "alg": "cg", "iters": wl.iters,
-                      "grouping": "48 contiguous readout subregions, one patch per group per line"},
-           "unit": "s/volume", "higher_is_better": False}
+    wl0 = synth.workload("3d224")
+    g0 = wl0.geom
+    rho = synth.phantom(g0.nx, g0.ny, g0.nz)
+    roi = torch.from_numpy(synth.roi_mask(rho)).to(dev)
+    coils = torch.from_numpy(synth.coil_maps(g0.nx, g0.ny, g0.nz, g0.nc, wl0.seed).astype(np.complex64)).to(dev)
+    rho_d = torch.from_numpy(rho.astype(np.complex64)).to(dev)
+    stream = torch.cuda.current_stream()
+    out = {"unit": "s/volume", "higher_is_better": False, "setup_s": None}
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    for prec, name in ((gpjc.FP32, "fp32"), (gpjc.BF16, "bf16")):
-        o = op if prec == gpjc.FP32 else gpjc.Operator(grp, coils, prec)
-        Sc = torch.empty((g.n_lines, plan.ntx_c), dtype=torch.complex64, device=dev)
-        x = torch.empty(g.shape, dtype=torch.complex64, device=dev)
-        e = _events(2)
-        grp.rebuild(coils, roi)  # warm-up of the group build
-        gpjc.compress(grp, S, prec, out=Sc)
-        e[0][0].record(stream)
-        grp.rebuild(coils, roi)
-        e[0][1].record(stream)
-        e[1][0].record(stream)
-        gpjc.compress(grp, S, prec, out=Sc)
-        e[1][1].record(stream)
-        for _ in range(3):
-            o.recon(Sc, alg=gpjc.CG, iters=wl.iters, out=x, sync=False)
-        ev = _events(3)
-        for a, b in ev:
-            a.record(stream)
-            o.recon(Sc, alg=gpjc.CG, iters=wl.iters, out=x, sync=False)
-            b.record(stream)
+    for name in ("3d224", "3d224r1"):
+        wl = synth.workload(name)
+        g = wl.geom
+        plan = gpjc.Plan(g)
+        grp = gpjc.Groups.build(plan, coils, roi)
+        op = gpjc.Operator(grp, coils)
+        S = op.simulate(rho_d)
+        gen = torch.Generator(device=dev).manual_seed(wl.seed)
+        S += wl.sigma / np.sqrt(2) * torch.complex(torch.randn(S.shape, generator=gen, device=dev),
+                                                   torch.randn(S.shape, generator=gen, device=dev))
         torch.cuda.synchronize()
-        rec = [a.elapsed_time(b) / 1e3 for a, b in ev]
-        res[name] = {"s_per_volume": round(statistics.median(rec), 4), "runs": 3, "warmup": 3,
-                     "groups_s": round(e[0][0].elapsed_time(e[0][1]) / 1e3, 4),
-                     "compress_s": round(e[1][0].elapsed_time(e[1][1]) / 1e3, 5),
-                     "pairs_per_s": round(wl.iters / statistics.median(rec), 2)}
-        if prec != gpjc.FP32:
-            del o
-    res["clocks"] = sampler.stop()
-    res["bf16_recon_speedup_vs_fp32"] = round(res["fp32"]["s_per_volume"] / res["bf16"]["s_per_volume"], 3)
-    res["setup_s"] = round(setup_s, 2)
+        res = {"config": {"workload": name, "matrix": [g.nz, g.ny, g.nx], "coils": g.nc, "os": g.os,
+                          "cycles": g.cycles, "groups": g.n_groups, "w": g.w, "keep": int(g.keep[0]),
+                          "ntx_c": int(plan.ntx_c), "n_lines": g.n_lines, "alg": "cg", "iters": wl.iters,
+                          "grouping": ("48 contiguous readout subregions, one patch per group per line"
+                                       if name == "3d224" else "48 groups per modulation period of 96 samples")}}
+        for prec, pname in ((gpjc.FP32, "fp32"), (gpjc.BF16, "bf16")):
+            o = op if prec == gpjc.FP32 else gpjc.Operator(grp, coils, prec)
+            Sc = torch.empty((g.n_lines, plan.ntx_c), dtype=torch.complex64, device=dev)
+            x = torch.empty(g.shape, dtype=torch.complex64, device=dev)
+            e = _events(2)
+            grp.rebuild(coils, roi)  # warm-up of the group build
+            gpjc.compress(grp, S, prec, out=Sc)
+            e[0][0].record(stream)
+            grp.rebuild(coils, roi)
+            e[0][1].record(stream)
+            e[1][0].record(stream)
+            gpjc.compress(grp, S, prec, out=Sc)
+            e[1][1].record(stream)
+            for _ in range(3):
+                o.recon(Sc, alg=gpjc.CG, iters=wl.iters, out=x, sync=False)
+            ev = _events(3)
+            for a, b in ev:
+                a.record(stream)
+                o.recon(Sc, alg=gpjc.CG, iters=wl.iters, out=x, sync=False)
+                b.record(stream)
+            torch.cuda.synchronize()
+            rec = [a.elapsed_time(b) / 1e3 for a, b in ev]
+            res[pname] = {"s_per_volume": round(statistics.median(rec), 4), "runs": 3, "warmup": 3,
+                          "groups_s": round(e[0][0].elapsed_time(e[0][1]) / 1e3, 4),
+                          "compress_s": round(e[1][0].elapsed_time(e[1][1]) / 1e3, 5),
+                          "pairs_per_s": round(wl.iters / statistics.median(rec), 2)}
+            if prec != gpjc.FP32:
+                del o
+        res["bf16_recon_speedup_vs_fp32"] = round(res["fp32"]["s_per_volume"] / res["bf16"]["s_per_volume"], 3)
+        out[name] = res
+        del op, grp, plan, S
+        torch.cuda.empty_cache()
+    out["clocks"] = sampler.stop()
+    out["setup_s"] = round(time.perf_counter() - t0, 2)
+    return out
+
+
+def run_local_b0(args, dev):
+    """Nonlinear local-B0 operator at the 256 x 256 size (32 coils, 8x
+    oversampling, 32 periodic groups, keep 16): stored compressed readout
+    matrices (256 rows x 4096 x 256 complex64 = 2.15 GB), built on the device
+    from three synthetic local-B0 fields; E_c + E_c^H pairs timed after
+    warm-up.  Each application streams the matrices from HBM once, so the
+    readout stages are HBM-bound: achieved GB/s = matrix bytes / stage time.
+    (Timing only: A_g comes from the wave model's group build, the same
+    shapes as a general-phase build.)"""
+    import numpy as np
+    import torch
+
+    from paper_2601_05418_gb300 import gpjc, synth
+
+    wl = synth.workload("2d256")
+    g = wl.geom
+    case = synth.make_case(wl, with_noise=False)
+    plan = gpjc.Plan(g)
+    coils = torch.from_numpy(case.coils.astype(np.complex64)).to(dev)
+    grp = gpjc.Groups.build(plan, coils, torch.from_numpy(case.roi).to(dev))
+    fields = torch.from_numpy(synth.local_b0_fields(g.nx, g.ny, 1, 3, 7).astype(np.float32)).to(dev)
+    amps = synth.local_b0_amplitudes(g.ntx, g.cycles, 3, 8)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    op = gpjc.Operator.local_b0(grp, coils, fields, amps)
+    build_s = time.perf_counter() - t0
+    x = torch.from_numpy(case.rho.astype(np.complex64)).to(dev).reshape(g.shape)
+    pairs = time_pairs(op, x, n=50, warm=5)
+    y = op.E(x)
+    z = op.EH(y)
+    torch.cuda.synchronize()
+    op.profile(True)  # resets the stage records; the pairs below are the measured ones
+    n = 20
+    for _ in range(n):
+        op.E(x, out=y)
+        op.EH(y, out=z)
+    torch.cuda.synchronize()
+    gbytes = 8.0 * g.ny * g.nz * plan.ntx_c * g.nx
+    res = {"config": {"workload": "2d256 local-B0", "matrix": [g.nz, g.ny, g.nx], "coils": g.nc, "os": g.os,
+                      "fields": 3, "ntx_c": int(plan.ntx_c), "stored_matrix_bytes": int(gbytes)},
+           "build_s": round(build_s, 3), "pairs_isolated": pairs}
+    peak = peaks()[0]["hbm_gbs"]
+    for s, nm in ((gpjc.STAGE_READOUT_FWD, "k_lb0_fwd"), (gpjc.STAGE_READOUT_ADJ, "k_lb0_adj")):
+        ms, cnt = op.profile_read(s)
+        per = ms / max(cnt, 1)
+        gbs = gbytes / (per * 1e-3) / 1e9
+        res[nm] = {"launch_ms": round(per, 4), "achieved_gbs": round(gbs, 1), "peak_gbs": peak,
+                   "frac": round(gbs / peak, 4), "bound": "hbm",
+                   "algorithmic_bytes": int(gbytes), "note": "matrix bytes only (vectors are < 0.1%)"}
+    op.profile(False)
     return res
 
 
