@@ -359,6 +359,27 @@ gpjc_status gpjc_batch_set_wait_budget(gpjc_batch* batch, int64_t cycles);
 /* Blocks of the persistent launch and work items of one reconstruction. */
 gpjc_status gpjc_batch_info(const gpjc_batch* batch, int32_t* grid, int64_t* items);
 
+/* ------------------------------------------------------------------ multi-slice graph -- */
+/* Many reconstructions in one CUDA graph (the batched form for slices of
+ * uneven size, coil count and precision, 2D or 3D): the slices'
+ * reconstructions (gpjc_recon's CG or decoupled CG, same recurrences and
+ * results) are captured on n_branches parallel branches and replayed with
+ * one graph launch, so one slice's small grids, tails and launch gaps are
+ * filled by the others.  Slices go longest first (rows x coils x N_tx) to the
+ * least-loaded branch.  Each operator appears once and must not be used
+ * elsewhere while the graph runs.  Creation makes the branch streams and
+ * events and allocates one status word per slice (synchronous). */
+typedef struct gpjc_multi gpjc_multi;
+gpjc_status gpjc_multi_create(int32_t n, gpjc_op* const* ops, int32_t n_branches, gpjc_multi** out);
+void gpjc_multi_destroy(gpjc_multi* multi);
+/* d_Sc[i] [n_lines_i][ntx_c_i] in, d_x[i] image out (x0 = 0), params as
+ * gpjc_recon (alg GPJC_CG or GPJC_DECOUPLED, use_x0 / use_graph ignored:
+ * always captured; the graph is cached for the same pointers and params, the
+ * first call also runs each slice once eagerly).  h_status (may be NULL):
+ * the worst device status after a synchronisation of `stream`. */
+gpjc_status gpjc_recon_multi(gpjc_multi* multi, const float* const* d_Sc, float* const* d_x,
+                             const gpjc_recon_params* params, int32_t* h_status, void* stream);
+
 /* ------------------------------------------------------------------ no allocation -- */
 /* x = E_c^H y without any allocation: the paper has no counterpart; this
  * entry point exists for callers that cannot call cudaMalloc on the path

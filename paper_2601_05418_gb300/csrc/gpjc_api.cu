@@ -255,7 +255,9 @@ static bool make_tc_geom(const gpjc_plan* p, int ebytes, TcGeom* t) {
   for (int q = 0; q < p->np; ++q)
     if (p->pg[q] != q % G) return false;
   const int n_occ = (int)(p->ntx / P);
-  if (128 % n_occ) return false;
+  // a tile holds lt = floor(128 / n_occ) lines; its last 128 - lt n_occ MMA
+  // rows are padding
+  if (n_occ > 128) return false;
   if (p->keep_max > 128 || w > 64) return false;
   if (((long long)P * ebytes) % 8 || ((long long)p->ntx * ebytes) % 8) return false;
   t->G = G; t->w = w; t->nc = p->nc; t->ns = p->ns; t->ntx = p->ntx; t->ntxc = p->ntxc;
@@ -1886,5 +1888,157 @@ extern "C" gpjc_status gpjc_batch_info(const gpjc_batch* b, int32_t* grid, int64
   if (!b) return fail(GPJC_EINVAL, "null batch");
   if (grid) *grid = b->grid;
   if (items) *items = b->stage_start.back();
+  return GPJC_OK;
+}
+
+// ------------------------------------------------------------------ multi-slice graph --
+// Many reconstructions (any operators: sizes, coil counts, precisions, 2D or
+// 3D, any algorithm) captured together in one CUDA graph whose slices run on
+// parallel branches: each branch runs its slices' reconstructions one after
+// another with the single-slice kernels, and the branches share the GPU, so
+// the launch gaps, small grids and tails of one slice are filled by the
+// others.  Slices are assigned longest first to the least-loaded branch
+// (cost: readout work rows x coils x N_tx).
+struct gpjc_multi {
+  int n, nb;
+  std::vector<gpjc_op*> ops;
+  std::vector<std::vector<int>> branch;  // slices of each branch, in order
+  std::vector<cudaStream_t> streams;     // one per branch
+  std::vector<cudaEvent_t> join;         // one per branch
+  cudaStream_t cs;
+  cudaEvent_t fork;
+  cudaGraphExec_t gexec;
+  std::vector<char> gkey;
+  int* d_status;                         // gathered per-slice status words
+  DevMem mem;
+  ~gpjc_multi() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (auto s : streams) cudaStreamDestroy(s);
+    for (auto e : join) cudaEventDestroy(e);
+    if (cs) cudaStreamDestroy(cs);
+    if (fork) cudaEventDestroy(fork);
+  }
+};
+
+extern "C" gpjc_status gpjc_multi_create(int32_t n, gpjc_op* const* ops, int32_t n_branches, gpjc_multi** out) {
+  if (!ops || !out || n < 1) return fail(GPJC_EINVAL, "need at least one operator");
+  if (n_branches < 1 || n_branches > 64) return fail(GPJC_EINVAL, "n_branches must be in [1, 64]");
+  *out = nullptr;
+  auto* m = new (std::nothrow) gpjc_multi();
+  if (!m) return fail(GPJC_ENOMEM, "host allocation");
+  m->cs = nullptr;
+  m->fork = nullptr;
+  m->gexec = nullptr;
+  std::unique_ptr<gpjc_multi> guard(m);
+  m->n = n;
+  m->nb = std::min<int>(n_branches, n);
+  m->ops.assign(ops, ops + n);
+  for (int i = 0; i < n; ++i) {
+    if (!ops[i]) return fail(GPJC_EINVAL, "operator %d is null", i);
+    for (int j = 0; j < i; ++j)
+      if (ops[j] == ops[i]) return fail(GPJC_EINVAL, "operator %d appears twice (its workspaces would race)", i);
+  }
+  // longest first onto the least-loaded branch
+  std::vector<std::pair<double, int>> cost(n);
+  for (int i = 0; i < n; ++i) {
+    const Geo& g = ops[i]->plan->geo;
+    cost[i] = {(double)g.rows * g.nc * g.ntx, i};
+  }
+  std::stable_sort(cost.begin(), cost.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  m->branch.assign(m->nb, {});
+  std::vector<double> load(m->nb, 0.0);
+  for (const auto& c : cost) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    m->branch[k].push_back(c.second);
+    load[k] += c.first;
+  }
+  m->streams.assign(m->nb, nullptr);
+  m->join.assign(m->nb, nullptr);
+  for (int k = 0; k < m->nb; ++k) {
+    CK(cudaStreamCreateWithFlags(&m->streams[k], cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&m->join[k], cudaEventDisableTiming));
+  }
+  CK(cudaStreamCreateWithFlags(&m->cs, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&m->fork, cudaEventDisableTiming));
+  gpjc_status s;
+  if ((s = m->mem.alloc(&m->d_status, (size_t)n))) return s;
+  *out = guard.release();
+  return GPJC_OK;
+}
+
+extern "C" void gpjc_multi_destroy(gpjc_multi* m) { delete m; }
+
+extern "C" gpjc_status gpjc_recon_multi(gpjc_multi* m, const float* const* d_Sc, float* const* d_x,
+                                        const gpjc_recon_params* params, int32_t* h_status, void* stream) {
+  if (!m || !d_Sc || !d_x || !params) return fail(GPJC_EINVAL, "null argument");
+  gpjc_recon_params rp = *params;
+  rp.use_x0 = 0;
+  rp.use_graph = 0;
+  if (rp.alg != GPJC_CG && rp.alg != GPJC_DECOUPLED)
+    return fail(GPJC_EUNSUPPORTED, "the multi-slice graph runs CG or the decoupled CG");
+  if (rp.iters < 0 || rp.iters > 100000) return fail(GPJC_EINVAL, "iters out of range");
+  std::vector<char> key(sizeof(rp) + 2 * sizeof(void*) * m->n);
+  memcpy(key.data(), &rp, sizeof(rp));
+  for (int i = 0; i < m->n; ++i) {
+    if (!d_Sc[i] || !d_x[i]) return fail(GPJC_EINVAL, "slice %d: null data pointer", i);
+    memcpy(key.data() + sizeof(rp) + 2 * sizeof(void*) * i, &d_Sc[i], sizeof(void*));
+    memcpy(key.data() + sizeof(rp) + 2 * sizeof(void*) * i + sizeof(void*), &d_x[i], sizeof(void*));
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!m->gexec || key != m->gkey) {
+    if (m->gexec) {
+      cudaGraphExecDestroy(m->gexec);
+      m->gexec = nullptr;
+    }
+    // every kernel attribute is set outside the capture by one eager pass of
+    // each slice (its result is overwritten by the graph launch below)
+    for (int i = 0; i < m->n; ++i) {
+      gpjc_status s = recon_body(m->ops[i], (const float2*)d_Sc[i], (float2*)d_x[i], rp, m->cs);
+      if (s) return s;
+    }
+    CK(cudaStreamSynchronize(m->cs));
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(m->cs, cudaStreamCaptureModeRelaxed));
+    g_capturing = true;
+    gpjc_status s = GPJC_OK;
+    cudaError_t ce = cudaEventRecord(m->fork, m->cs);
+    for (int k = 0; k < m->nb && ce == cudaSuccess && !s; ++k) {
+      ce = cudaStreamWaitEvent(m->streams[k], m->fork, 0);
+      for (int i : m->branch[k]) {
+        if (ce != cudaSuccess || s) break;
+        s = recon_body(m->ops[i], (const float2*)d_Sc[i], (float2*)d_x[i], rp, m->streams[k]);
+        if (!s) ce = cudaMemcpyAsync(m->d_status + i, m->ops[i]->status, sizeof(int), cudaMemcpyDeviceToDevice,
+                                     m->streams[k]);
+      }
+      if (ce == cudaSuccess) ce = cudaEventRecord(m->join[k], m->streams[k]);
+      if (ce == cudaSuccess) ce = cudaStreamWaitEvent(m->cs, m->join[k], 0);
+    }
+    g_capturing = false;
+    const cudaError_t ee = cudaStreamEndCapture(m->cs, &graph);
+    if (s) {
+      if (ee == cudaSuccess) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (ee == cudaSuccess) cudaGraphDestroy(graph);
+      return fail(GPJC_ECUDA, "multi-slice graph capture: %s",
+                  cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    ce = cudaGraphInstantiate(&m->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) return fail(GPJC_ECUDA, "multi-slice graph: %s", cudaGetErrorString(ce));
+    m->gkey = key;
+  }
+  CK(cudaGraphLaunch(m->gexec, st));
+  note_launches(1);
+  if (h_status) {
+    std::vector<int> v(m->n, 0);
+    CK(cudaMemcpyAsync(v.data(), m->d_status, sizeof(int) * m->n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int worst = 0;
+    for (int i = 0; i < m->n; ++i) worst = std::max(worst, v[i]);
+    *h_status = worst == kDevNonFinite ? GPJC_ENONFINITE : (worst ? GPJC_ETIMEOUT : GPJC_OK);
+    if (worst) return fail((gpjc_status)*h_status, "multi-slice reconstruction device status %d", worst);
+  }
   return GPJC_OK;
 }

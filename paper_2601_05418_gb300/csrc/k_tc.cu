@@ -296,8 +296,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
   uint32_t ph_ld = 0, ph_mma = 0;
   bool ok = true;
   uint64_t* stuck = nullptr;
-  const int m = tid;  // A row = output column (line l, occurrence q)
-  const int l = m / t.n_occ, q = m - l * t.n_occ;
+  const int m = tid;  // A row = output column (line l, occurrence q); rows >= lt n_occ are padding
+  const bool mrow = m < t.lt * t.n_occ;
+  const int l = mrow ? m / t.n_occ : 0, q = mrow ? m - (m / t.n_occ) * t.n_occ : 0;
   for (int c = 0; c < t.nchunks && ok; ++c) {
     if (tid == 0) {
       mbar_expect_tx(&bars[0], (uint32_t)t.stg_tx + bbytes);
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
       break;
     }
     // staging -> 16-bit core image (row m holds its column's samples of the chunk)
-    for (int nl = 0; nl < t.ncc; ++nl) {
+    for (int nl = 0; nl < t.ncc && mrow; ++nl) {
       const size_t base = ((size_t)(l * t.ncc + nl) * t.n_occ + q) * t.box0 + shift;
       for (int tau = 0; tau < t.w; ++tau) {
         uint32_t pk, pl = 0u;
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
         if (NI == 2) *(uint32_t*)(Al + core_off(m, k, t.Kc)) = pl;
       }
     }
-    for (int k = 2 * t.ncc * t.w; k < t.Kc; k += 2) {
+    for (int k = mrow ? 2 * t.ncc * t.w : 0; k < t.Kc; k += 2) {
       *(uint32_t*)(At + core_off(m, k, t.Kc)) = 0u;
       if (NI == 2) *(uint32_t*)(Al + core_off(m, k, t.Kc)) = 0u;
     }
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
     // epilogue: lane m of TMEM holds column m; 8 fp32 columns = 4 complex values per load
     const int line = l0 + l;
     const int p = (g * t.w + q * t.P) / t.w;
-    const bool valid = line < n_lines;
+    const bool valid = mrow && line < n_lines;
     const float s = t.scale[g];
     const int keep = t.keep[g];
     float2* o = out + (size_t)line * t.ntxc + (valid ? t.poff[p] : 0);
@@ -410,11 +411,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_expand(TcGeom t, const flo
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(tmem_slot, 256);
-  const int m = tid;
-  const int l = m / t.n_occ, q = m - l * t.n_occ;
+  const int m = tid;  // rows >= lt n_occ of the tile are padding
+  const bool mrow = m < t.lt * t.n_occ;
+  const int l = mrow ? m / t.n_occ : 0, q = mrow ? m - (m / t.n_occ) * t.n_occ : 0;
   const int row = r0 + l;
   const int p = (g * t.w + q * t.P) / t.w;
-  const bool valid = row < n_rows;
+  const bool valid = mrow && row < n_rows;
   const int keep = t.keep[g];
   const float2* h = H + (size_t)(valid ? row : 0) * t.ntxc + t.poff[p];
   for (int k = 0; k < t.Kx / 2; ++k) {

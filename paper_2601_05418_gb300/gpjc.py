@@ -104,6 +104,9 @@ _sig("gpjc_query", [_P, C.c_int32, C.c_int32, _I32P, C.POINTER(C.c_uint64)])
 _sig("gpjc_debug_fail_allocations", [C.c_int64], None)
 _sig("gpjc_probe_fp32_tflops", [C.c_int32, C.POINTER(C.c_double)])
 _sig("gpjc_op_create_local_b0", [_P, _P, C.c_int32, _P, _P, C.POINTER(_P)])
+_sig("gpjc_multi_create", [C.c_int32, C.POINTER(_P), C.c_int32, C.POINTER(_P)])
+_sig("gpjc_multi_destroy", [_P], None)
+_sig("gpjc_recon_multi", [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(ReconParams), _I32P, _P])
 _sig("gpjc_batch_create", [C.c_int32, C.POINTER(_P), C.c_int32, C.POINTER(_P)])
 _sig("gpjc_batch_destroy", [_P], None)
 _sig("gpjc_recon_batched", [_P, C.POINTER(_P), C.POINTER(_P), C.c_int32, _I32P, _P])
@@ -494,6 +497,34 @@ class Batch:
         st = C.c_int32(0)
         check(_lib.gpjc_recon_batched(self.h, sp, xp, 1 if use_graph else 0, C.byref(st) if sync else None,
                                       _stream(stream)))
+        return xs, st.value
+
+
+class Multi:
+    """Many reconstructions (any operators) in one CUDA graph on parallel
+    branches (gpjc_multi_create / gpjc_recon_multi)."""
+
+    def __init__(self, ops: Sequence[Operator], n_branches: int = 8):
+        self.ops = list(ops)
+        arr = (_P * len(self.ops))(*[op.h for op in self.ops])
+        self.h = _P()
+        check(_lib.gpjc_multi_create(len(self.ops), arr, int(n_branches), C.byref(self.h)))
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _lib.gpjc_multi_destroy(self.h)
+            self.h = None
+
+    def recon(self, Scs: Sequence[torch.Tensor], xs: Optional[Sequence[torch.Tensor]] = None, alg: int = CG,
+              iters: int = 30, sync: bool = True, stream=None):
+        if xs is None:
+            xs = [torch.empty(op.image_shape, dtype=torch.complex64, device=Sc.device)
+                  for op, Sc in zip(self.ops, Scs)]
+        sp = (_P * len(Scs))(*[_dptr(t, torch.complex64) for t in Scs])
+        xp = (_P * len(xs))(*[_dptr(t, torch.complex64) for t in xs])
+        rp = ReconParams(alg, iters, 0.0, 0.0, 0, 0, 0, 1, 0.0, 1e-3)
+        st = C.c_int32(0)
+        check(_lib.gpjc_recon_multi(self.h, sp, xp, C.byref(rp), C.byref(st) if sync else None, _stream(stream)))
         return xs, st.value
 
 

@@ -88,3 +88,42 @@ def test_batched_cg_wait_budget_runs_out(gp):
     assert status == 0
     g, op, Sc, x_ref = sl[0]
     check_image(to_np(xs[0]), x_ref, 1e-5)
+
+
+def test_multi_slice_graph_matches_single_slice_and_oracle(gp):
+    """The multi-slice graph (slices on parallel branches of one CUDA graph)
+    runs each slice's reconstruction with the single-slice kernels: the images
+    are bit-identical to gpjc_recon's, and within the FP32 bound of the
+    oracle; a 3D slice and a BF16 slice ride along."""
+    iters = 12
+    sl = make_slices(gp, iters)
+    wl = synth.workload("3d56")
+    g3 = wl.geom
+    c3 = synth.make_case(wl)
+    As3, _, _ = O.build_groups(g3, c3.coils, c3.roi)
+    Sc3 = O.compress(g3, As3, O.simulate(g3, c3.coils, c3.rho, c3.noise))
+    x3_ref, _ = O.reconstruct(g3, c3.coils, As3, Sc3, "cg", iters)
+    op3 = gp.Operator(gp.Groups.from_matrices(gp.Plan(g3), As3), to_dev(c3.coils))
+    g, op0, Sc0, x0_ref = sl[2]
+    op16 = gp.Operator(op0.groups, op0.coil, gp.BF16)
+    ops = [s[1] for s in sl] + [op3, op16]
+    scs = [s[2] for s in sl] + [to_dev(Sc3), Sc0]
+    refs = [s[3] for s in sl] + [x3_ref, x0_ref]
+    multi = gp.Multi(ops, n_branches=3)
+    xs, status = multi.recon(scs, iters=iters)
+    assert status == 0
+    for k, (op, sc, xm, ref) in enumerate(zip(ops, scs, xs, refs)):
+        x1, _ = op.recon(sc, alg=gp.CG, iters=iters, use_graph=False)
+        torch.cuda.synchronize()
+        assert torch.equal(xm, x1), k
+        check_image(to_np(xm), ref, 1e-5 if op is not op16 else 1e-3, f"multi slice {k}")
+    # replay of the cached graph gives the same images
+    xs2, status = multi.recon(scs, xs, iters=iters)
+    assert status == 0 and all(torch.equal(a, b) for a, b in zip(xs, xs2))
+
+
+def test_multi_slice_graph_rejects_a_repeated_operator(gp):
+    sl = make_slices(gp, 2)
+    with pytest.raises(gp.GpjcError) as ei:
+        gp.Multi([sl[0][1], sl[1][1], sl[0][1]])
+    assert ei.value.status == gp.GPJC_EINVAL
