@@ -331,7 +331,7 @@ def run_gpjc(args, rank, world, local):
                 "unit": "TFLOP/s", "frac": round(achieved / alu_peak, 4), "traffic": traffic,
                 "peak_source": "measured: FP32 FMA loop on this device (gpjc_probe_fp32_tflops, SM count x 8 "
                                "blocks x 256 threads x 8 chains), taken just before the timed region",
-                "launch_ms": round(dom_ms, 5), "flop_per_launch": int(fl),
+                "launch_ms": round(dom_ms, 5), "flop_per_launch": int(fl), "tuning": list(op.tuning()),
                 "stage_share": {names[s]: round(prof[s][0] / max(total_ms, 1e-9), 4) for s in prof}}
     if not fp32:
         roofline["alu_work"] = ("coil multiply, pre / post factors and readout FFTs; the A_g contraction "
@@ -387,7 +387,8 @@ def run_gpjc(args, rank, world, local):
             b16()
         torch.cuda.synchronize()
         rank_barrier(world)
-        ta16, tb16 = timed_steps(a16, b16, args.steps)
+        prof16 = {s: [0.0, 0] for s in prof}
+        ta16, tb16 = timed_steps(a16, b16, args.steps, op16, prof16)
         rank_barrier(world)
         op16.profile(False)
         ms16 = max_over_ranks(sum(ta16) + sum(tb16), world, dev)
@@ -403,6 +404,11 @@ def run_gpjc(args, rank, world, local):
                 "recon_speedup_vs_fp32": round(recon_ms / rc16, 3),
                 "recon_pairs_per_s": round(job_rate(pairs_per_step, args.steps, world, rc16), 2),
                 "pairs_isolated": time_pairs(op16, xin),
+                "tuning": list(op16.tuning()),
+                "stage_ms_per_launch": {nm: round(prof16[s][0] / max(prof16[s][1], 1), 5) for s, nm in
+                                        ((gpjc.STAGE_READOUT_FWD, "readout_fwd (k1_sim_fwd2 + k_tc_compress)"),
+                                         (gpjc.STAGE_PHASE_ENCODE, "phase_encode (k2)"),
+                                         (gpjc.STAGE_READOUT_ADJ, "readout_adj (k_tc_expand + k1_sim_adj2)"))},
                 "nrmse_vs_fp32_image": float(f"{nr:.3e}"),
                 "note": "same workload, inputs, stage events and timing as the FP32 step (BF16 operands as "
                         "head + remainder, three MMAs per K step); NRMSE against the FP64 oracle is checked "

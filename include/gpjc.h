@@ -281,6 +281,16 @@ gpjc_status gpjc_op_create_local_b0(const gpjc_groups* groups, const float* d_co
  * (the FP32 spectra of one piece stay in L2; the results do not depend on
  * the split).  *nchunk receives the forward chunk count (may be NULL). */
 gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchunk);
+/* The operator's current launch knobs (set at creation or by
+ * gpjc_op_autotune): coil chunks of the forward and of the adjoint readout
+ * stage, row pieces of the 16-bit adjoint.  Any output may be NULL. */
+gpjc_status gpjc_op_tuning(const gpjc_op* op, int32_t* nchunk, int32_t* nchunk_adj, int32_t* adj_pieces);
+/* Sets those knobs (e.g. from a persisted autotuning result): nchunk in
+ * [1, the forward workspace's planes], nchunk_adj in [1, the adjoint's],
+ * adj_pieces in [1, 8]; results do not depend on them beyond FP32 rounding
+ * order.  GPJC_EINVAL outside the ranges, GPJC_EUNSUPPORTED for the
+ * stored-matrix operator.  Host only. */
+gpjc_status gpjc_op_set_tuning(gpjc_op* op, int32_t nchunk, int32_t nchunk_adj, int32_t adj_pieces);
 
 /* y = E_c x (Eq. 15): d_x [nz][ny][nx] -> d_y [n_lines][ntx_c]. */
 gpjc_status gpjc_apply_E(const gpjc_op* op, const float* d_x, float* d_y, void* stream);

@@ -265,7 +265,11 @@ static bool make_tc_geom(const gpjc_plan* p, int ebytes, TcGeom* t) {
   int c0 = 1;
   while ((2 * w * c0) % 16) ++c0;
   int ncc = c0;
-  while (ncc + c0 <= p->nc && 2 * w * (ncc + c0) <= 128) ncc += c0;
+  // K chunks of at most 64 (unless one chunk of c0 coils is longer): the
+  // staging, the (split) operand images and the A_g images of a chunk stay
+  // near 80 KB, so two blocks share an SM and one block's TMA load overlaps
+  // the other's conversion and MMAs
+  while (ncc + c0 <= p->nc && 2 * w * (ncc + c0) <= 64) ncc += c0;
   t->ncc = ncc;
   t->nchunks = (p->nc + ncc - 1) / ncc;
   t->Kc = 2 * w * ncc;
@@ -1318,6 +1322,32 @@ static gpjc_status time_normal(gpjc_op* op, cudaStream_t st, cudaEvent_t e0, cud
     float t = 0.f;
     CK(cudaEventElapsedTime(&t, e0, e1));
     *ms = std::min(*ms, t);
+  }
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_op_tuning(const gpjc_op* op, int32_t* nchunk, int32_t* nchunk_adj, int32_t* adj_pieces) {
+  if (!op) return fail(GPJC_EINVAL, "null operator");
+  if (nchunk) *nchunk = op->nchunk;
+  if (nchunk_adj) *nchunk_adj = op->nchunk_a;
+  if (adj_pieces) *adj_pieces = op->adj_pieces;
+  return GPJC_OK;
+}
+
+extern "C" gpjc_status gpjc_op_set_tuning(gpjc_op* op, int32_t nchunk, int32_t nchunk_adj, int32_t adj_pieces) {
+  if (!op) return fail(GPJC_EINVAL, "null operator");
+  if (op->lb0_G) return fail(GPJC_EUNSUPPORTED, "the stored-matrix operator has fixed launch knobs");
+  if (nchunk < 1 || nchunk > op->nchunk_max) return fail(GPJC_EINVAL, "nchunk must be in [1, %d]", op->nchunk_max);
+  if (nchunk_adj < 1 || nchunk_adj > op->nchunk_a_max)
+    return fail(GPJC_EINVAL, "nchunk_adj must be in [1, %d]", op->nchunk_a_max);
+  if (adj_pieces < 1 || adj_pieces > kMaxAdjPieces) return fail(GPJC_EINVAL, "adj_pieces must be in [1, %d]", kMaxAdjPieces);
+  op->nchunk = nchunk;
+  op->nchunk_a = nchunk_adj;
+  op->adj_pieces = adj_pieces;
+  if (op->gexec) {
+    cudaGraphExecDestroy(op->gexec);
+    op->gexec = nullptr;
+    op->gkey.clear();
   }
   return GPJC_OK;
 }

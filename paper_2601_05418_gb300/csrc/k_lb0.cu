@@ -124,8 +124,22 @@ __global__ void __launch_bounds__(kLbThreads) k_lb0_adj(int nx, int ntxc, int ro
   float2* red = hs + jper;
   if (s < nsub) {
     float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-    for (int j = j0 + s; j < j1; j += nsub) {
-      const float4 gv = __ldcs(reinterpret_cast<const float4*>(G + ((size_t)row * ntxc + j) * nx) + q);
+    const float4* g4 = reinterpret_cast<const float4*>(G + (size_t)row * ntxc * nx) + q;
+    int j = j0 + s;
+    // four independent 16-byte loads in flight per thread
+    for (; j + 3 * nsub < j1; j += 4 * nsub) {
+      float4 gv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) gv[u] = __ldcs(g4 + (size_t)(j + u * nsub) * half);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 h = hs[j + u * nsub - j0];
+        cfmac(a0, make_float2(gv[u].x, gv[u].y), h);
+        cfmac(a1, make_float2(gv[u].z, gv[u].w), h);
+      }
+    }
+    for (; j < j1; j += nsub) {
+      const float4 gv = __ldcs(g4 + (size_t)j * half);
       const float2 h = hs[j - j0];
       cfmac(a0, make_float2(gv.x, gv.y), h);
       cfmac(a1, make_float2(gv.z, gv.w), h);

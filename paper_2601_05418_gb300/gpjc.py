@@ -105,6 +105,8 @@ _sig("gpjc_debug_fail_allocations", [C.c_int64], None)
 _sig("gpjc_probe_fp32_tflops", [C.c_int32, C.POINTER(C.c_double)])
 _sig("gpjc_op_create_local_b0", [_P, _P, C.c_int32, _P, _P, C.POINTER(_P)])
 _sig("gpjc_multi_create", [C.c_int32, C.POINTER(_P), C.c_int32, C.POINTER(_P)])
+_sig("gpjc_op_tuning", [_P, _I32P, _I32P, _I32P])
+_sig("gpjc_op_set_tuning", [_P, C.c_int32, C.c_int32, C.c_int32])
 _sig("gpjc_multi_destroy", [_P], None)
 _sig("gpjc_recon_multi", [_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(ReconParams), _I32P, _P])
 _sig("gpjc_batch_create", [C.c_int32, C.POINTER(_P), C.c_int32, C.POINTER(_P)])
@@ -389,6 +391,44 @@ class Operator:
         n = C.c_int32()
         check(_lib.gpjc_op_autotune(self.h, _stream(stream), C.byref(n)))
         return n.value
+
+    def tuning(self):
+        """(forward coil chunks, adjoint coil chunks, adjoint row pieces)."""
+        a, b, c = C.c_int32(), C.c_int32(), C.c_int32()
+        check(_lib.gpjc_op_tuning(self.h, C.byref(a), C.byref(b), C.byref(c)))
+        return a.value, b.value, c.value
+
+    def set_tuning(self, nchunk: int, nchunk_adj: int, adj_pieces: int) -> None:
+        check(_lib.gpjc_op_set_tuning(self.h, int(nchunk), int(nchunk_adj), int(adj_pieces)))
+
+    def shape_class(self) -> str:
+        """Key of the operator's shape class for persisted tuning results."""
+        g = self.plan.geom
+        return (f"{g.nz}x{g.ny}x{g.nx}_c{g.nc}_os{g.os}_w{g.w}_G{g.n_groups}_k{int(max(g.keep))}"
+                f"_l{g.n_lines}_p{self.precision}")
+
+    def autotune_cached(self, path: str, stream=None):
+        """gpjc_op_autotune with a JSON cache of the chosen knobs per shape
+        class: a cached class is set directly, a new one is timed and
+        stored.  Returns the knobs."""
+        import json
+        import os
+
+        cache = {}
+        if os.path.exists(path):
+            with open(path) as f:
+                cache = json.load(f)
+        key = self.shape_class()
+        if key in cache:
+            self.set_tuning(*cache[key])
+        else:
+            self.autotune(stream)
+            cache[key] = list(self.tuning())
+            tmp = path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+            os.replace(tmp, path)
+        return self.tuning()
 
     def E(self, x: torch.Tensor, out=None, stream=None) -> torch.Tensor:
         if out is None:

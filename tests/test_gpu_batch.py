@@ -127,3 +127,34 @@ def test_multi_slice_graph_rejects_a_repeated_operator(gp):
     with pytest.raises(gp.GpjcError) as ei:
         gp.Multi([sl[0][1], sl[1][1], sl[0][1]])
     assert ei.value.status == gp.GPJC_EINVAL
+
+
+def test_uneven_batch_workload_sizes_vs_oracle(gp):
+    """Slices of the uneven batch workload itself (matrix 192-320, 16-32
+    coils, 6-8x oversampling, 16-48 groups; the two with the least readout
+    work, so the oracle finishes in seconds): the persistent batch and the
+    multi-slice graph against the FP64 oracle, CG-SENSE 5 iterations."""
+    iters = 5
+    wls = synth.batch_workloads(64)
+    wls = sorted(wls, key=lambda w: w.geom.nx * w.geom.ny * w.geom.nc * w.geom.os)[:2]
+    ops, scs, refs = [], [], []
+    for wl in wls:
+        g = wl.geom
+        assert 192 <= g.nx <= 320 and 16 <= g.nc <= 32
+        coils = synth.coil_maps(g.nx, g.ny, 1, g.nc, wl.seed)
+        rho = synth.phantom(g.nx, g.ny)
+        roi = synth.roi_mask(rho)
+        S = O.simulate(g, coils, rho, synth.complex_normal((g.n_lines, g.nc, g.ntx), wl.seed + 1, wl.sigma))
+        As, _, _ = O.build_groups(g, coils, roi)
+        Sc = O.compress(g, As, S)
+        x_ref, _ = O.reconstruct(g, coils, As, Sc, "cg", iters)
+        ops.append(gp.Operator(gp.Groups.from_matrices(gp.Plan(g), As), to_dev(coils)))
+        scs.append(to_dev(Sc))
+        refs.append(x_ref)
+    xb, status = gp.Batch(ops, iters).recon(scs)
+    assert status == 0
+    xm, status = gp.Multi(ops, n_branches=2).recon(scs, iters=iters)
+    assert status == 0
+    for a, b, ref in zip(xb, xm, refs):
+        check_image(to_np(a), ref, 1e-5, "persistent batch, uneven-batch slice")
+        check_image(to_np(b), ref, 1e-5, "multi-slice graph, uneven-batch slice")
