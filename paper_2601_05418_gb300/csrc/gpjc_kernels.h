@@ -22,6 +22,9 @@ cudaError_t launch_k1_adj_fp32(const Geo& g, const float2* H2, const float2* coi
                                float2* xpart, int nchunk, cudaStream_t st);
 cudaError_t launch_sim_fwd(const Geo& g, const float2* x, const float2* coil, float2* V, int nchunk,
                            cudaStream_t st);
+// rows [row0, row0 + nrows) only
+cudaError_t launch_sim_fwd_rows(const Geo& g, const float2* x, const float2* coil, float2* V, int nchunk, int row0,
+                                int nrows, cudaStream_t st);
 cudaError_t launch_sim_adj(const Geo& g, const float2* V, const float2* coil, float2* xpart, int nchunk,
                            cudaStream_t st);
 // gradient of the smoothed isotropic TV of each z-slice (k_tv.cu)
@@ -68,8 +71,9 @@ size_t tc_pack_comp_elems(const TcGeom& t, int fmt);  // uint16 elements of all 
 size_t tc_pack_exp_elems(const TcGeom& t, int fmt);   // uint16 elements of all expansion images
 cudaError_t launch_tc_pack(const TcGeom& t, int fmt, const float2* A, const float* scale, uint16_t* Bc,
                            uint16_t* Bx, cudaStream_t st);
+// lines [line0, lines) (line0 a multiple of the tile's line count)
 cudaError_t launch_tc_compress(const CUtensorMap& map, const TcGeom& t, int fmt, int src_bytes, const uint16_t* Bc,
-                               float2* out, int lines, int* status, cudaStream_t st);
+                               float2* out, int line0, int lines, int* status, cudaStream_t st);
 cudaError_t launch_tc_expand(const TcGeom& t, int fmt, const float2* H, const uint16_t* Bx, float2* V, int rows,
                              int* status, cudaStream_t st);
 size_t tc_gram2_smem(const Geo& g);
@@ -77,7 +81,7 @@ cudaError_t launch_tc_gram2(const Geo& g, const float2* chat, const int* pix, co
                             const int* pref, const int2* cpairs, int npairs, double2* P, int* status,
                             cudaStream_t st);
 cudaError_t launch_sim_fwd_f16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
-                               cudaStream_t st);
+                               int row0, int nrows, cudaStream_t st);
 cudaError_t launch_sim_adj_f16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,
                                cudaStream_t st);
 

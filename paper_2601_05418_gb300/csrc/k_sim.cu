@@ -61,12 +61,12 @@ __device__ __forceinline__ float2 post_of(const Geo& g, int t, int row) {
 template <typename VT>
 __global__ void __launch_bounds__(kK1Threads) k1_sim_fwd(Geo g, const float2* __restrict__ x,
                                                          const float2* __restrict__ coil,
-                                                         VT* __restrict__ V, int cpc) {
+                                                         VT* __restrict__ V, int cpc, int row0) {
   extern __shared__ float2 smem[];
   float2* A = smem;
   float2* B = A + spad_size(g.ntx);
   float2* tw = B + spad_size(g.ntx);
-  const int row = blockIdx.x, chunk = blockIdx.y;
+  const int row = row0 + blockIdx.x, chunk = blockIdx.y;
   for (int i = threadIdx.x; i < g.nx; i += blockDim.x) tw[i] = g.tw_x[i];
   const size_t L = (size_t)g.rows * g.nx;
   const int nx = g.nx, os = g.os;
@@ -151,7 +151,7 @@ static size_t sim2_smem(const Geo& g) {
 template <typename VT, int NB>
 __global__ void __launch_bounds__(kK1Threads) k1_sim_fwd2(Geo g, const float2* __restrict__ x,
                                                           const float2* __restrict__ coil,
-                                                          VT* __restrict__ V, int cpc) {
+                                                          VT* __restrict__ V, int cpc, int row0) {
   static_assert(NB >= 1 && NB <= kSimMaxNB, "one or two coils per FFT call");
   extern __shared__ float2 smem[];
   const int nx = g.nx, os = g.os, ntx = g.ntx;
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kK1Threads) k1_sim_fwd2(Geo g, const float2* _
   float2* B = O + spad_size(NB * ntx);  // FFT scratch
   float2* u = B + NB * ntx;             // c_n x of the NB coils
   float2* tw = u + NB * nx;
-  const int row = blockIdx.x, chunk = blockIdx.y;
+  const int row = row0 + blockIdx.x, chunk = blockIdx.y;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = g.tw_x[i];
   const size_t L = (size_t)g.rows * nx;
   const float2* xrow = x + (size_t)row * nx;
@@ -263,10 +263,10 @@ static bool sim_two_pass(const Geo& g) {
 
 template <typename VT, int NB>
 static cudaError_t launch_sim_fwd2(const Geo& g, const float2* x, const float2* coil, VT* V, int cpc, dim3 grid,
-                                   cudaStream_t st) {
+                                   int row0, cudaStream_t st) {
   const size_t sm = sim2_smem<NB>(g);
   cudaFuncSetAttribute(k1_sim_fwd2<VT, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  note_launches(1); k1_sim_fwd2<VT, NB><<<grid, kK1Threads, sm, st>>>(g, x, coil, V, cpc);
+  note_launches(1); k1_sim_fwd2<VT, NB><<<grid, kK1Threads, sm, st>>>(g, x, coil, V, cpc, row0);
   return cudaGetLastError();
 }
 
@@ -279,15 +279,16 @@ static cudaError_t launch_sim_adj2(const Geo& g, const VT* V, const float2* coil
   return cudaGetLastError();
 }
 
+// rows [row0, row0 + nrows) of the forward readout
 template <typename VT>
 static cudaError_t launch_sim_fwd_t(const Geo& g, const float2* x, const float2* coil, VT* V, int nchunk,
-                                    cudaStream_t st) {
+                                    int row0, int nrows, cudaStream_t st) {
   const int cpc = (g.nc + nchunk - 1) / nchunk;
-  dim3 grid(g.rows, nchunk);
-  if (sim_two_pass(g)) return launch_sim_fwd2<VT, 2>(g, x, coil, V, cpc, grid, st);
+  dim3 grid(nrows, nchunk);
+  if (sim_two_pass(g)) return launch_sim_fwd2<VT, 2>(g, x, coil, V, cpc, grid, row0, st);
   const size_t sm = sim_smem(g);
   cudaFuncSetAttribute(k1_sim_fwd<VT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  note_launches(1); k1_sim_fwd<VT><<<grid, kK1Threads, sm, st>>>(g, x, coil, V, cpc);
+  note_launches(1); k1_sim_fwd<VT><<<grid, kK1Threads, sm, st>>>(g, x, coil, V, cpc, row0);
   return cudaGetLastError();
 }
 
@@ -315,11 +316,15 @@ static cudaError_t launch_sim_adj_t(const Geo& g, const VT* V, const float2* coi
 
 cudaError_t launch_sim_fwd(const Geo& g, const float2* x, const float2* coil, float2* V, int nchunk,
                            cudaStream_t st) {
-  return launch_sim_fwd_t<float2>(g, x, coil, V, nchunk, st);
+  return launch_sim_fwd_t<float2>(g, x, coil, V, nchunk, 0, g.rows, st);
+}
+cudaError_t launch_sim_fwd_rows(const Geo& g, const float2* x, const float2* coil, float2* V, int nchunk, int row0,
+                                int nrows, cudaStream_t st) {
+  return launch_sim_fwd_t<float2>(g, x, coil, V, nchunk, row0, nrows, st);
 }
 cudaError_t launch_sim_fwd_f16(const Geo& g, const float2* x, const float2* coil, void* V, int nchunk,
-                               cudaStream_t st) {
-  return launch_sim_fwd_t<__half2>(g, x, coil, (__half2*)V, nchunk, st);
+                               int row0, int nrows, cudaStream_t st) {
+  return launch_sim_fwd_t<__half2>(g, x, coil, (__half2*)V, nchunk, row0, nrows, st);
 }
 cudaError_t launch_sim_adj_f16(const Geo& g, const void* V, const float2* coil, float2* xpart, int nchunk,
                                cudaStream_t st) {

@@ -264,14 +264,14 @@ __global__ void k_tc_pack_exp(TcGeom t, const float2* __restrict__ A, const floa
 template <int FMT, int SRC_BYTES>
 __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_constant__ CUtensorMap tmap, TcGeom t,
                                                               const uint16_t* __restrict__ Bpk,
-                                                              float2* __restrict__ out, int n_lines,
-                                                              int* status) {
+                                                              float2* __restrict__ out, int line0,
+                                                              int n_lines, int* status) {
   // BF16 splits the FP32 source into head + remainder (16-bit sources are FP16 only)
   static_assert(FMT == 0 || SRC_BYTES == 4, "the BF16 compression takes FP32 sources");
   constexpr int NI = tc_images(FMT);
   extern __shared__ __align__(1024) unsigned char tsm[];
   const int g = blockIdx.y;
-  const int l0 = blockIdx.x * t.lt;
+  const int l0 = line0 + blockIdx.x * t.lt;
   unsigned char* stg = tsm;                                   // staging [lt][ncc][n_occ][box0]
   uint16_t* At = (uint16_t*)(tsm + t.stg_bytes);              // 128 x Kc core image (head)
   uint16_t* Al = At + (NI - 1) * 128 * t.Kc;                  // 128 x Kc remainder (BF16)
@@ -563,23 +563,24 @@ cudaError_t launch_tc_pack(const TcGeom& t, int fmt, const float2* A, const floa
 
 template <int FMT, int SB>
 static cudaError_t launch_comp_t(const CUtensorMap& map, const TcGeom& t, const uint16_t* Bc, float2* out,
-                                 int lines, int* status, cudaStream_t st) {
+                                 int line0, int lines, int* status, cudaStream_t st) {
   const size_t sm = tc_compress_smem(t, FMT);
   static size_t attr = 0;
   if (sm > attr) {
     cudaFuncSetAttribute(k_tc_compress<FMT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = sm;
   }
-  dim3 grid((lines + t.lt - 1) / t.lt, t.G);
-  note_launches(1); k_tc_compress<FMT, SB><<<grid, kTcThreads, sm, st>>>(map, t, Bc, out, lines, status);
+  dim3 grid((lines - line0 + t.lt - 1) / t.lt, t.G);
+  note_launches(1); k_tc_compress<FMT, SB><<<grid, kTcThreads, sm, st>>>(map, t, Bc, out, line0, lines, status);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_compress(const CUtensorMap& map, const TcGeom& t, int fmt, int src_bytes, const uint16_t* Bc,
-                               float2* out, int lines, int* status, cudaStream_t st) {
-  if (fmt == 1 && src_bytes == 4) return launch_comp_t<1, 4>(map, t, Bc, out, lines, status, st);
-  if (fmt == 0 && src_bytes == 4) return launch_comp_t<0, 4>(map, t, Bc, out, lines, status, st);
-  if (fmt == 0 && src_bytes == 2) return launch_comp_t<0, 2>(map, t, Bc, out, lines, status, st);
+                               float2* out, int line0, int lines, int* status, cudaStream_t st) {
+  if (line0 < 0 || line0 >= lines || line0 % t.lt) return cudaErrorInvalidValue;
+  if (fmt == 1 && src_bytes == 4) return launch_comp_t<1, 4>(map, t, Bc, out, line0, lines, status, st);
+  if (fmt == 0 && src_bytes == 4) return launch_comp_t<0, 4>(map, t, Bc, out, line0, lines, status, st);
+  if (fmt == 0 && src_bytes == 2) return launch_comp_t<0, 2>(map, t, Bc, out, line0, lines, status, st);
   return cudaErrorInvalidValue;
 }
 

@@ -110,8 +110,11 @@ int main() {
   const int cpc = (nc + nchunk - 1) / nchunk;
   for (int r = 0; r < rows; ++r)
     for (int c = 0; c < nchunk; ++c) {
-      run_block(r, c, [&] { k1_sim_fwd2<float2, 2>(g, x.data(), coil.data(), V.data(), cpc); });
-      run_block(r, c, [&] { k1_sim_adj2<float2, 2, 1>(g, W.data(), coil.data(), xpart.data(), cpc, 0); });
+      run_block(r, c, [&] { k1_sim_fwd2<float2, 2>(g, x.data(), coil.data(), V.data(), cpc, 0); });
+      if (nx <= 256)  // one output pixel per thread, as the library launches it
+        run_block(r, c, [&] { k1_sim_adj2<float2, 2, 1>(g, W.data(), coil.data(), xpart.data(), cpc, 0); });
+      else
+        run_block(r, c, [&] { k1_sim_adj2<float2, 2, 2>(g, W.data(), coil.data(), xpart.data(), cpc, 0); });
     }
   for (auto& v : V) printf("%.9e %.9e\n", v.x, v.y);
   for (size_t i = 0; i < L; ++i) {
@@ -130,8 +133,13 @@ def _flat(a):
 
 
 @pytest.mark.skipif(shutil.which("g++") is None or not os.path.isdir(CUDA_INC), reason="needs g++ and CUDA headers")
-def test_two_coil_readout_model_kernels_match_oracle(tmp_path):
-    nx, ny, nc, os_, nchunk, cycles, kappa = 40, 6, 3, 2, 2, 2.0, 1.3
+@pytest.mark.parametrize("nx,ny,os_", [(40, 6, 2), (320, 2, 8)])
+def test_two_coil_readout_model_kernels_match_oracle(tmp_path, nx, ny, os_):
+    """40 points (8 x 5) at 2x, one output pixel per thread; 320 points
+    (16 x 20) at 8x: 16 transforms of 20 rows exceed the 256 threads (two
+    tasks per thread in the FFT passes) and the adjoint keeps two output
+    pixels per thread."""
+    nc, nchunk, cycles, kappa = 3, 2, 2.0, 1.3
     src = tmp_path / "sim_driver.cpp"
     src.write_text(DRIVER)
     exe = tmp_path / "sim_driver"
