@@ -19,12 +19,39 @@
 // are listed on the host per geometry and RB (plan tables), so any patch ->
 // group map and any per-group keep are handled by the same kernels.
 #pragma once
+#include <algorithm>
+#include <cstdlib>
 #include "gpjc_device.cuh"
 #include "gpjc_kernels.h"
 
 namespace gpjc {
 
 constexpr int kRThreads = 256;
+
+// Preferred shared-memory carveout (percent of the maximum) of a readout
+// kernel with `smem` bytes per block: just enough for the blocks its
+// registers allow per SM, so the rest of the unified L1 / shared memory
+// caches A_g and the factor tables (the forward kernel, limited to two
+// blocks by its registers, gains ~5%; the adjoint keeps its three blocks).
+// GPJC_READOUT_CARVEOUT (0..100) overrides it.
+inline int readout_carveout(const void* func, size_t smem) {
+  if (const char* e = getenv("GPJC_READOUT_CARVEOUT")) {
+    const int c = atoi(e);
+    if (c >= 0 && c <= 100) return c;
+  }
+  cudaFuncAttributes fa;
+  int dev = 0, smem_sm = 0;
+  if (cudaFuncGetAttributes(&fa, func) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+      fa.numRegs <= 0 || smem_sm <= 0) {
+    cudaGetLastError();
+    return 100;
+  }
+  const int by_regs = 65536 / (fa.numRegs * kRThreads);
+  const size_t need = (size_t)std::max(by_regs, 1) * (smem + 1024);
+  const int pct = (int)((need * 100 + (size_t)smem_sm - 1) / (size_t)smem_sm);
+  return std::min(100, std::max(pct, 1));
+}
 
 // logical row stride of the spectra in shared memory (multiple of 8, so a
 // row's padded sub-buffer starts at spad(r * stride))
@@ -145,6 +172,7 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
 #pragma unroll
       for (int c = 0; c < 4; ++c) upair = upair && (uoff[m][c] < 0 || (uoff[m][c] & 7) == 0);
       if (upair) {
+#pragma unroll 2
         for (int tau = 0; tau < w; tau += 2) {
           float2 a0[4], a1[4], u0[4], u1[4];
           {
@@ -276,6 +304,7 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
       const float2* Ap = Arow + h.x + n * w;
       // full tiles with 16-byte aligned rows load two samples at a time
       const bool vec = h.z == TS && (ns & 1) == 0 && (((uintptr_t)Ap) & 15) == 0;
+#pragma unroll 2
       for (int k = 0; k < h.y; ++k) {
         float2 a[TS], hv[4];
         if (vec) {

@@ -12,7 +12,8 @@ static cudaError_t launch_a(const Geo& g, const RTiles& tl, const float2* H2, co
   static int attr = 0;
   if ((int)sm > attr) {
     cudaFuncSetAttribute(k1a_tiled<MAXX, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k1a_tiled<MAXX, TS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k1a_tiled<MAXX, TS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         readout_carveout((const void*)k1a_tiled<MAXX, TS>, sm));
     attr = (int)sm;
   }
   dim3 grid((g.rows + tl.rb - 1) / tl.rb, nchunk);

@@ -67,7 +67,8 @@ static cudaError_t launch_f(const Geo& g, const RTiles& tl, const float2* x, con
   static int attr = 0;
   if ((int)sm > attr) {
     cudaFuncSetAttribute(k1f_tiled<MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(k1f_tiled<MAXT>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k1f_tiled<MAXT>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         readout_carveout((const void*)k1f_tiled<MAXT>, sm));
     attr = (int)sm;
   }
   dim3 grid((g.rows + tl.rb - 1) / tl.rb, nchunk);
