@@ -606,9 +606,10 @@ static gpjc_status groups_compute(gpjc_groups* gr, const float2* coil, const uin
   CK(launch_eig_matmul(g, b, gr->P, X, Y, st));           // Z = P Q
   CK(launch_eig_project(g, b, X, Y, gr->Hm, st));         // Q^H P Q
   CK(launch_eig_jacobi(g, b, gr->Hm, gr->W, gr->ritz, gr->order, 60, st));
-  CK(launch_eig_rotate(g, b, X, gr->W, gr->order, gr->U, st));  // Ritz vectors, descending
-  CK(launch_eig_matmul(g, b, gr->P, gr->U, Y, st));       // P U
-  CK(launch_eig_residual(g, b, Y, gr->U, gr->ritz, gr->order, gr->resid, st));
+  CK(launch_eig_rotate(g, b, X, gr->W, gr->order, gr->U, st));  // Ritz vectors U = Q W, descending
+  // P U = (P Q) W = Z W: the same rotation of Z (b^2 instead of N_s^2 work per column)
+  CK(launch_eig_rotate(g, b, Y, gr->W, gr->order, X, st));
+  CK(launch_eig_residual(g, b, X, gr->U, gr->ritz, gr->order, gr->resid, st));
   CK(launch_form_A(g, b, gr->U, h_T ? gr->dT : nullptr, gr->A, gr->AT, gr->scale, st));
   gr->host_valid = false;
   return groups_pack_tc(gr, st);

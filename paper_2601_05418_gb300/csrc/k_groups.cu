@@ -733,10 +733,14 @@ cudaError_t launch_eig_project(const Geo& g, int b, const double2* Q, const doub
 // (descending, ties by index).
 __global__ void __launch_bounds__(256) k_eig_jacobi(int b, double2* __restrict__ Hm, double2* __restrict__ W,
                                                     double* __restrict__ ritz, int* __restrict__ order,
-                                                    int max_sweeps) {
+                                                    int max_sweeps, int wsm) {
   extern __shared__ double2 jsm[];
   const int n = b + (b & 1);  // even player count (a dummy when b is odd)
   double2* H = jsm;           // [b][b]
+  const int grp_ = blockIdx.x;
+  // rotations accumulate in shared memory when H and W fit there together
+  // (written to W at the end), else directly in W
+  double2* Ws = wsm ? jsm + b * b : W + (size_t)grp_ * b * b;
   __shared__ int perm[kEigMaxB + 2];
   __shared__ int pp[kEigMaxB / 2 + 1], pq[kEigMaxB / 2 + 1];
   __shared__ double pc[kEigMaxB / 2 + 1], ps[kEigMaxB / 2 + 1];
@@ -756,7 +760,7 @@ __global__ void __launch_bounds__(256) k_eig_jacobi(int b, double2* __restrict__
       v.y = 0.0;
     }
     H[i] = v;
-    Wg[i] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+    Ws[i] = make_double2(r == c ? 1.0 : 0.0, 0.0);
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = i;
   __syncthreads();
@@ -831,10 +835,10 @@ __global__ void __launch_bounds__(256) k_eig_jacobi(int b, double2* __restrict__
         double2 cp = H[r * b + p], cq = H[r * b + q];
         H[r * b + p] = zsub(zscale(cp, c), zscale(zmulc(e, cq), s));
         H[r * b + q] = zadd(zscale(zmul(e, cp), s), zscale(cq, c));
-        cp = Wg[(size_t)r * b + p];
-        cq = Wg[(size_t)r * b + q];
-        Wg[(size_t)r * b + p] = zsub(zscale(cp, c), zscale(zmulc(e, cq), s));
-        Wg[(size_t)r * b + q] = zadd(zscale(zmul(e, cp), s), zscale(cq, c));
+        cp = Ws[r * b + p];
+        cq = Ws[r * b + q];
+        Ws[r * b + p] = zsub(zscale(cp, c), zscale(zmulc(e, cq), s));
+        Ws[r * b + q] = zadd(zscale(zmul(e, cp), s), zscale(cq, c));
       }
       __syncthreads();
       for (int k = threadIdx.x; k < half; k += blockDim.x) {
@@ -857,6 +861,8 @@ __global__ void __launch_bounds__(256) k_eig_jacobi(int b, double2* __restrict__
     }
   }
   for (int c = threadIdx.x; c < b; c += blockDim.x) ritz[(size_t)grp * b + c] = H[c * b + c].x;
+  if (wsm)
+    for (int i = threadIdx.x; i < b * b; i += blockDim.x) Wg[i] = Ws[i];
   __syncthreads();
   for (int c = threadIdx.x; c < b; c += blockDim.x) {
     const double v = H[c * b + c].x;
@@ -872,9 +878,10 @@ __global__ void __launch_bounds__(256) k_eig_jacobi(int b, double2* __restrict__
 cudaError_t launch_eig_jacobi(const Geo& g, int b, double2* Hm, double2* W, double* ritz, int* order,
                               int max_sweeps, cudaStream_t st) {
   if (b > kEigMaxB) return cudaErrorInvalidValue;
-  const size_t sm = sizeof(double2) * (size_t)b * b;
+  const int wsm = 2 * sizeof(double2) * (size_t)b * b <= (size_t)200 * 1024 ? 1 : 0;
+  const size_t sm = (wsm ? 2 : 1) * sizeof(double2) * (size_t)b * b;
   cudaFuncSetAttribute(k_eig_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  note_launches(1); k_eig_jacobi<<<g.G, 256, sm, st>>>(b, Hm, W, ritz, order, max_sweeps);
+  note_launches(1); k_eig_jacobi<<<g.G, 256, sm, st>>>(b, Hm, W, ritz, order, max_sweeps, wsm);
   return cudaGetLastError();
 }
 
