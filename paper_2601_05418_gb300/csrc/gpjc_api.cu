@@ -160,7 +160,11 @@ struct gpjc_plan {
   Geo geo;
   RTiles rt_f, rt_a;  // register-tiled readout stage (rb == 0: use the per-output kernels)
   bool tc_ok;          // tensor-core compression available (periodic group map, sizes in range)
-  TcGeom tc32, tc16;   // for FP32 sources (raw data) and 16-bit sources (hybrid data)
+  // tensor-core geometries: BF16 with FP32 sources (raw data and the BF16
+  // operator's spectra; split operands), FP16 with FP32 sources (raw data),
+  // FP16 with FP16 sources (the FP16 operator's spectra).  The two FP16 ones
+  // share their K chunking, so each format has one set of packed A_g images.
+  TcGeom tc32b, tc32h, tc16;
   // aliased sets of the mask (hybrid-space reconstruction, Sec. 3.4): set of
   // each phase-encode row (raster z, y), sets numbered by their first row;
   // CSR member lists (rows ascending) on the host and the device
@@ -247,7 +251,7 @@ static void aliased_sets(int ny, int nz, const std::vector<int>& ky, const std::
 
 // Tensor-core compression geometry for sources of `ebytes` bytes per real
 // element; false when the group map or the sizes do not fit the kernels.
-static bool make_tc_geom(const gpjc_plan* p, int ebytes, TcGeom* t) {
+static bool make_tc_geom(const gpjc_plan* p, int ebytes, int fmt, TcGeom* t) {
   memset(t, 0, sizeof *t);
   const int G = p->G, w = p->w;
   const long long P = (long long)G * w;
@@ -265,11 +269,17 @@ static bool make_tc_geom(const gpjc_plan* p, int ebytes, TcGeom* t) {
   int c0 = 1;
   while ((2 * w * c0) % 16) ++c0;
   int ncc = c0;
-  // K chunks of at most 64 (unless one chunk of c0 coils is longer): the
-  // staging, the (split) operand images and the A_g images of a chunk stay
-  // near 80 KB, so two blocks share an SM and one block's TMA load overlaps
-  // the other's conversion and MMAs
-  while (ncc + c0 <= p->nc && 2 * w * (ncc + c0) <= 64) ncc += c0;
+  // K chunks of at most 64 for FP16, 32 for the split BF16 GEMM (unless one
+  // chunk of c0 coils is longer): a block's staging and operand images stay
+  // small, so several blocks share an SM and one block's TMA load overlaps
+  // the others' conversion and MMAs (2d256 BF16 forward: K chunks of
+  // 128 / 64 / 32: 197 / 158 / 146 us; FP16: 132 / 121 / 127 us)
+  int kmax = fmt == 1 ? 32 : 64;  // GPJC_TC_KMAX (16..256) overrides the K chunk cap
+  if (const char* e = getenv("GPJC_TC_KMAX")) {
+    const int v = atoi(e);
+    if (v >= 16 && v <= 256) kmax = v;
+  }
+  while (ncc + c0 <= p->nc && 2 * w * (ncc + c0) <= kmax) ncc += c0;
   t->ncc = ncc;
   t->nchunks = (p->nc + ncc - 1) / ncc;
   t->Kc = 2 * w * ncc;
@@ -284,8 +294,7 @@ static bool make_tc_geom(const gpjc_plan* p, int ebytes, TcGeom* t) {
   t->Kx = ((2 * p->keep_max + 15) / 16) * 16;
   t->nexp = ((2 * p->ns + 15) / 16) * 16;
   if (t->box0 > 256 || ncc > 256 || t->lt > 256 || n_occ > 256) return false;
-  // FP32 sources serve the split BF16 compression (two images per operand)
-  if (tc_compress_smem(*t, ebytes == 4 ? 1 : 0) > 220 * 1024 || tc_expand_smem(*t, 1) > 220 * 1024) return false;
+  if (tc_compress_smem(*t, fmt) > 220 * 1024 || tc_expand_smem(*t, fmt) > 220 * 1024) return false;
   return true;
 }
 
@@ -417,11 +426,13 @@ extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
     return s;
   CK(launch_make_tables(g, tw_x, tw_y, tw_z, pre, ay, az, p->cycles, p->kappa_y, p->kappa_z, 0));
   CK(launch_make_post(g, post_y, post_z, p->cycles, p->kappa_y, p->kappa_z, 0));
-  p->tc_ok = make_tc_geom(p, 4, &p->tc32) && make_tc_geom(p, 2, &p->tc16);
+  p->tc_ok = make_tc_geom(p, 4, 1, &p->tc32b) && make_tc_geom(p, 4, 0, &p->tc32h) && make_tc_geom(p, 2, 0, &p->tc16);
   if (p->tc_ok) {
-    p->tc32.keep = p->tc16.keep = d_keep;
-    p->tc32.aoff = p->tc16.aoff = d_aoff;
-    p->tc32.poff = p->tc16.poff = d_poff;
+    for (TcGeom* t : {&p->tc32b, &p->tc32h, &p->tc16}) {
+      t->keep = d_keep;
+      t->aoff = d_aoff;
+      t->poff = d_poff;
+    }
   }
   // register-tile tables of the readout stage: the smallest rows-per-block
   // that gives every thread of a block a tile, within the shared-memory and
@@ -544,11 +555,12 @@ static gpjc_status groups_alloc_A(gpjc_groups* gr) {
   gr->tc_bc[0] = gr->tc_bc[1] = gr->tc_bx[0] = gr->tc_bx[1] = nullptr;
   gr->tc_status = nullptr;
   if (p->tc_ok) {
-    const TcGeom& t = p->tc16;
-    for (int f = 0; f < 2; ++f)
+    for (int f = 0; f < 2; ++f) {
+      const TcGeom& t = f ? p->tc32b : p->tc16;  // the chunking of the format's packs
       if ((s = gr->mem.alloc(&gr->tc_bc[f], tc_pack_comp_elems(t, f))) ||
           (s = gr->mem.alloc(&gr->tc_bx[f], tc_pack_exp_elems(t, f))))
         return s;
+    }
     if ((s = gr->mem.alloc(&gr->tc_status, 1))) return s;
     CK(cudaMemset(gr->tc_status, 0, sizeof(int)));
   }
@@ -559,9 +571,12 @@ static gpjc_status groups_alloc_A(gpjc_groups* gr) {
 static gpjc_status groups_pack_tc(gpjc_groups* gr, cudaStream_t st) {
   const gpjc_plan* p = gr->plan;
   if (!p->tc_ok) return GPJC_OK;
-  TcGeom t = p->tc16;  // the packs depend only on N, K and chunking, shared by both sources
-  t.scale = gr->scale;
-  for (int f = 0; f < 2; ++f) CK(launch_tc_pack(t, f, gr->A, gr->scale, gr->tc_bc[f], gr->tc_bx[f], st));
+  for (int f = 0; f < 2; ++f) {
+    // the packs depend only on N, K and the format's chunking
+    TcGeom t = f ? p->tc32b : p->tc16;
+    t.scale = gr->scale;
+    CK(launch_tc_pack(t, f, gr->A, gr->scale, gr->tc_bc[f], gr->tc_bx[f], st));
+  }
   return GPJC_OK;
 }
 
@@ -860,7 +875,7 @@ extern "C" gpjc_status gpjc_compress(const gpjc_groups* gr, const float* d_S, fl
   const gpjc_plan* p = gr->plan;
   if (!p->tc_ok) return fail(GPJC_EUNSUPPORTED, "tensor-core compression needs a periodic group map");
   if (((uintptr_t)d_S) & 15) return fail(GPJC_EINVAL, "d_S must be 16-byte aligned");
-  TcGeom t = p->tc32;
+  TcGeom t = prec == GPJC_BF16 ? p->tc32b : p->tc32h;
   t.scale = gr->scale;
   CUtensorMap map;
   if (!make_tc_tmap(t, d_S, g.n_lines, 4, &map)) return fail(GPJC_ECUDA, "cuTensorMapEncodeTiled failed");
@@ -1080,7 +1095,7 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
     if ((s = m.alloc(&v16, z.spectra))) return s;
     op->V16 = v16;
     const bool f32src = prec == GPJC_BF16;
-    if (!make_tc_tmap(f32src ? p->tc32 : p->tc16, op->V16, g.rows, f32src ? 4 : 2, &op->map16))
+    if (!make_tc_tmap(f32src ? p->tc32b : p->tc16, op->V16, g.rows, f32src ? 4 : 2, &op->map16))
       return fail(GPJC_ECUDA, "cuTensorMapEncodeTiled failed");
   }
   op->gexec = nullptr;
@@ -1162,7 +1177,7 @@ static cudaError_t readout_fwd(const gpjc_op* op, const float2* x, cudaStream_t 
     // BF16: FP32 spectra, split into head + remainder by the compression GEMM;
     // FP16: FP16 spectra, one rounding
     const int fmt = op->prec == GPJC_BF16 ? 1 : 0;
-    TcGeom t = fmt ? p->tc32 : p->tc16;
+    TcGeom t = fmt ? p->tc32b : p->tc16;
     t.scale = op->gr->scale;
     // one piece of all rows: smaller pieces keep their spectra in L2 but
     // launch fewer blocks each, which cost more on the 256 x 256 workload

@@ -209,9 +209,22 @@ __global__ void __launch_bounds__(kK1Threads) k1_sim_adj2(Geo g, const VT* __res
   for (int n = n0; n < n1; n += NB) {
     const int nb = min(NB, n1 - n);
     const VT* vin = V + ((size_t)row * g.nc + n) * ntx;
-    for (int i = threadIdx.x; i < nb * ntx; i += blockDim.x) {
-      const int t = i >= ntx ? i - ntx : i;
-      O[spad(i)] = cmulc(post_of(g, t, row), load_v<VT>(vin + i));
+    // loads first, four elements per thread at a time, so their latencies overlap
+    for (int i0 = threadIdx.x; i0 < nb * ntx; i0 += 4 * blockDim.x) {
+      float2 v[4], p[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < nb * ntx) {
+          v[u] = load_v<VT>(vin + i);
+          p[u] = post_of(g, i >= ntx ? i - ntx : i, row);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u * blockDim.x;
+        if (i < nb * ntx) O[spad(i)] = cmulc(p[u], v[u]);
+      }
     }
     __syncthreads();
     auto ld = [&](int f, int m) {
@@ -226,12 +239,23 @@ __global__ void __launch_bounds__(kK1Threads) k1_sim_adj2(Geo g, const VT* __res
     for (int j = 0; j < MAXX; ++j) {
       const int xx = threadIdx.x + j * kK1Threads;
       if (xx < nx) {
-        for (int c = 0; c < nb; ++c) {
-          float2 uu = make_float2(0.f, 0.f);
-          const float2* R = O + c * ntx;
-          for (int s = 0; s < os; ++s) cfmac(uu, __ldg(g.pre + s * nx + xx), R[s * nx + xx]);
-          cfmac(xacc[j], __ldg(coil + (n + c) * L + (size_t)row * nx + xx), uu);
+        float2 cv[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          cv[c] = c < nb ? __ldg(coil + (n + c) * L + (size_t)row * nx + xx) : make_float2(0.f, 0.f);
+        float2 uu[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) uu[c] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int s = 0; s < os; ++s) {
+          const float2 pr = __ldg(g.pre + s * nx + xx);  // shared by the NB coils
+#pragma unroll
+          for (int c = 0; c < NB; ++c)
+            if (c < nb) cfmac(uu[c], pr, O[c * ntx + s * nx + xx]);
         }
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          if (c < nb) cfmac(xacc[j], cv[c], uu[c]);
       }
     }
     __syncthreads();
