@@ -54,6 +54,11 @@ def parse():
                     help="skip the BF16 tensor-core step timed beside the FP32 one (2d256)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 3d224 and batch64 workloads timed after the 2d256 line")
+    ap.add_argument("--profile-case", default=None, choices=["fp32", "bf16", "fp16", "lb0", "recon16"],
+                    help="profiling driver: E_c + E_c^H pairs (or the BF16 FISTA recon) of the 2d256 operator "
+                         "between cudaProfilerStart / Stop, for ncu --profile-from-start off")
+    ap.add_argument("--reps", type=int, default=3, help="pairs (or recons) of --profile-case")
+    ap.add_argument("--knobs", default=None, help="--profile-case: forward chunks, adjoint chunks, adjoint pieces")
     return ap.parse_args()
 
 
@@ -954,9 +959,62 @@ def run_torch_floor(args):
     print(json.dumps(out), flush=True)
 
 
+def run_profile_case(args):
+    """The operator in a fixed configuration (no autotuning, so an
+    instrumented run uses the same launch knobs as a plain one), warmed up,
+    then `--reps` E_c + E_c^H pairs (or BF16 FISTA-50 recons) between
+    cudaProfilerStart and cudaProfilerStop."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as ge
+
+    ge.build()
+    from paper_2601_05418_gb300 import gpjc, synth
+
+    dev = torch.device("cuda", 0)
+    wl = synth.workload("2d256")
+    g = wl.geom
+    case = synth.make_case(wl)
+    plan = gpjc.Plan(g)
+    coils = torch.from_numpy(case.coils.astype(np.complex64)).to(dev)
+    grp = gpjc.Groups.build(plan, coils, torch.from_numpy(case.roi).to(dev))
+    x = torch.from_numpy(case.rho.astype(np.complex64)).to(dev).reshape(g.shape)
+    mode = args.profile_case
+    if mode == "lb0":
+        fields = torch.from_numpy(synth.local_b0_fields(g.nx, g.ny, 1, 3, 7).astype(np.float32)).to(dev)
+        op = gpjc.Operator.local_b0(grp, coils, fields, synth.local_b0_amplitudes(g.ntx, g.cycles, 3, 8))
+    else:
+        prec = {"fp32": gpjc.FP32, "bf16": gpjc.BF16, "fp16": gpjc.FP16, "recon16": gpjc.BF16}[mode]
+        op = gpjc.Operator(grp, coils, prec)
+        if args.knobs:
+            op.set_tuning(*[int(v) for v in args.knobs.split(",")])
+    y = op.E(x)
+    z = op.EH(y)
+    Sc = None
+    if mode == "recon16":
+        Sc = gpjc.compress(grp, gpjc.Operator(grp, coils).simulate(x), gpjc.BF16)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for _ in range(args.reps):
+        if Sc is not None:
+            op.recon(Sc, alg=gpjc.FISTA, iters=50, lam=1e-3, power_iters=20, haar_levels=4, use_graph=False)
+        else:
+            op.E(x, out=y)
+            op.EH(y, out=z)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"profile_case": mode, "reps": args.reps,
+                      "knobs": list(op.tuning()) if mode != "lb0" else None}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_info()
+    if args.profile_case:
+        if rank == 0:
+            run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
