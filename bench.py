@@ -45,7 +45,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpjc", choices=["gpjc", "reference"])
-    ap.add_argument("--workload", default="2d256", choices=["2d256", "2d256h", "2d256bf", "2d128", "batch64"])
+    ap.add_argument("--workload", default="2d256",
+                    choices=["2d256", "2d256h", "2d256bf", "2d128", "batch64", "3d224", "3d224r1"],
+                    help="3d224 / 3d224r1 only with --profile-case (the default line times both 3D workloads)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--torch-floor", action="store_true",
@@ -55,8 +57,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 3d224 and batch64 workloads timed after the 2d256 line")
     ap.add_argument("--profile-case", default=None, choices=["fp32", "bf16", "fp16", "lb0", "recon16"],
-                    help="profiling driver: E_c + E_c^H pairs (or the BF16 FISTA recon) of the 2d256 operator "
-                         "between cudaProfilerStart / Stop, for ncu --profile-from-start off")
+                    help="profiling driver: E_c + E_c^H pairs (or the BF16 FISTA recon) of the --workload "
+                         "operator between cudaProfilerStart / Stop, for ncu --profile-from-start off")
     ap.add_argument("--reps", type=int, default=3, help="pairs (or recons) of --profile-case")
     ap.add_argument("--knobs", default=None, help="--profile-case: forward chunks, adjoint chunks, adjoint pieces")
     return ap.parse_args()
@@ -319,7 +321,7 @@ def run_gpjc(args, rank, world, local):
 
     # ---- dominant kernel and its roofline (FP32 ALU bound)
     fp32 = prec == gpjc.FP32
-    names = {gpjc.STAGE_READOUT_FWD: ("k1f_tiled (coil x image, readout FFT, wave PSF, A_g)" if fp32 else
+    names = {gpjc.STAGE_READOUT_FWD: ("k1f_batched (coil x image, readout FFTs of 2 coils per call, wave PSF, A_g)" if fp32 else
                                       "k1_sim_fwd2 + k_tc_compress (readout spectra, tcgen05 A_g)"),
              gpjc.STAGE_PHASE_ENCODE: "k2 (phase-encode FFT / mask projection)",
              gpjc.STAGE_READOUT_ADJ: ("k1a_tiled (A_g^H, inverse readout FFT, coil sum)" if fp32 else
@@ -973,14 +975,22 @@ def run_profile_case(args):
     from paper_2601_05418_gb300 import gpjc, synth
 
     dev = torch.device("cuda", 0)
-    wl = synth.workload("2d256")
+    wl = synth.workload(args.workload)
     g = wl.geom
-    case = synth.make_case(wl)
-    plan = gpjc.Plan(g)
-    coils = torch.from_numpy(case.coils.astype(np.complex64)).to(dev)
-    grp = gpjc.Groups.build(plan, coils, torch.from_numpy(case.roi).to(dev))
-    x = torch.from_numpy(case.rho.astype(np.complex64)).to(dev).reshape(g.shape)
     mode = args.profile_case
+    if g.nz > 1:
+        if mode not in ("fp32", "bf16", "fp16"):
+            raise SystemExit("--profile-case: the 3D workloads take fp32, bf16 or fp16")
+        rho = synth.phantom(g.nx, g.ny, g.nz)
+        roi = synth.roi_mask(rho)
+        coil_np = synth.coil_maps(g.nx, g.ny, g.nz, g.nc, wl.seed)
+    else:
+        case = synth.make_case(wl)
+        rho, roi, coil_np = case.rho, case.roi, case.coils
+    plan = gpjc.Plan(g)
+    coils = torch.from_numpy(coil_np.astype(np.complex64)).to(dev)
+    grp = gpjc.Groups.build(plan, coils, torch.from_numpy(roi).to(dev))
+    x = torch.from_numpy(rho.astype(np.complex64)).to(dev).reshape(g.shape)
     if mode == "lb0":
         fields = torch.from_numpy(synth.local_b0_fields(g.nx, g.ny, 1, 3, 7).astype(np.float32)).to(dev)
         op = gpjc.Operator.local_b0(grp, coils, fields, synth.local_b0_amplitudes(g.ntx, g.cycles, 3, 8))
@@ -1004,7 +1014,7 @@ def run_profile_case(args):
             op.EH(y, out=z)
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
-    print(json.dumps({"profile_case": mode, "reps": args.reps,
+    print(json.dumps({"profile_case": mode, "workload": args.workload, "reps": args.reps,
                       "knobs": list(op.tuning()) if mode != "lb0" else None}), flush=True)
 
 
@@ -1015,6 +1025,8 @@ def main():
         if rank == 0:
             run_profile_case(args)
         return
+    if args.workload.startswith("3d"):
+        raise SystemExit("--workload 3d224 / 3d224r1 go with --profile-case; the default line times both")
     if args.impl == "reference":
         run_reference(args, rank, world)
         return

@@ -221,7 +221,11 @@ gpjc_status gpjc_compress(const gpjc_groups* groups, const float* d_S, float* d_
  * prec: GPJC_FP32 applies A_g with FP32 FFMA inside the fused readout
  * kernels; GPJC_BF16 / GPJC_FP16 write the readout spectra (FP32 for BF16,
  * whose GEMM splits them into head + remainder; FP16 for FP16) and apply
- * A_g / A_g^H as tensor-core GEMMs (periodic group maps).  Allocates the
+ * A_g / A_g^H as tensor-core GEMMs (periodic group maps) when patches are at
+ * least 8 samples wide (w >= 8); narrower patches (e.g. per-period groups of
+ * w = 2) keep the FP32 readout kernels, whose fused contraction is cheaper
+ * there than the tensor-core GEMMs and their spectra round trip through HBM
+ * (environment GPJC_TC_READOUT=0 / 1 forces either).  Allocates the
  * gpjc_query workspace; GPJC_ENOMEM (and nothing left allocated) when a
  * device allocation fails.  Synchronous. */
 gpjc_status gpjc_op_create(const gpjc_groups* groups, const float* d_coil, gpjc_precision prec, int32_t nchunk,
@@ -231,7 +235,7 @@ gpjc_status gpjc_op_create(const gpjc_groups* groups, const float* d_coil, gpjc_
  * receives N'_tx (the row length of S' and of the hybrid matrix), and
  * *workspace_bytes the device bytes gpjc_op_create(groups, ..., prec,
  * nchunk, ...) would allocate (hybrid matrices, partial images, CG / FISTA
- * vectors, scalars and, for BF16 / FP16, the spectra buffer).  Either
+ * vectors, scalars and, for BF16 / FP16 with w >= 8, the spectra buffer).  Either
  * output may be NULL.  Host only, no device work.  GPJC_EINVAL for bad
  * arguments, GPJC_EUNSUPPORTED where gpjc_op_create would refuse the
  * precision. */
@@ -276,7 +280,7 @@ gpjc_status gpjc_op_create_local_b0(const gpjc_groups* groups, const float* d_co
                                     const float* d_fields, const double* h_amps, gpjc_op** out);
 /* Times the readout-stage coil-chunk choices on `stream` and keeps the
  * fastest (synchronous): the adjoint's chunk count, then the forward's, and
- * for GPJC_BF16 / GPJC_FP16 operators the number of row pieces (1, 2, 4, 8)
+ * for tensor-core readouts (BF16 / FP16, w >= 8) the number of row pieces (1, 2, 4, 8)
  * in which the adjoint's tensor-core expansion and inverse readout FFT run
  * (the FP32 spectra of one piece stay in L2; the results do not depend on
  * the split).  *nchunk receives the forward chunk count (may be NULL). */

@@ -16,8 +16,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpjc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["gpjc_api.cu", "k_operator.cu", "k_pe.cu", "k_sim.cu", "k_readout_f.cu", "k_readout_a.cu",
-           "k_readout_a2.cu", "k_batch.cu", "k_tc.cu", "k_groups.cu", "k_recon.cu", "k_tv.cu", "k_probe.cu", "k_lb0.cu"]
+SOURCES = ["gpjc_api.cu", "k_operator.cu", "k_pe.cu", "k_sim.cu", "k_readout_f.cu", "k_readout_f2.cu",
+           "k_readout_a.cu", "k_readout_a2.cu", "k_batch.cu", "k_tc.cu", "k_groups.cu", "k_recon.cu", "k_tv.cu", "k_probe.cu", "k_lb0.cu"]
 
 
 def nvcc() -> str:

@@ -298,6 +298,38 @@ static bool make_tc_geom(const gpjc_plan* p, int ebytes, int fmt, TcGeom* t) {
   return true;
 }
 
+// Coils per step of the batched-transform forward readout kernel
+// (k1f_batched): the nb in 1..4 whose two FFT passes (nb rb os N2 and
+// nb rb os N1 tasks) keep the largest share of the block's 256 threads busy
+// per round, among those whose shared memory leaves room for two blocks per
+// SM (the kernel's registers allow two); the smaller nb on ties.  0 keeps the
+// per-row kernel (lengths without a two-pass plan, or nothing fits).
+// GPJC_READOUT_NB (0..4) overrides.  On the 256 x 256, 32-coil workload nb = 2
+// (one row, 16 transforms) took the forward stage from 179 to 157 us; on the
+// 224 x 224 x 160 volume nb = 1 with the block's 2 or 4 rows batched saved
+// 13-15%.  (The adjoint keeps its per-row kernel: a batched version with the
+// second pass in place in the FFT scratch measured 6-20% slower there.)
+static int pick_readout_nb(const Geo& g, const RTiles& rt) {
+  if (g.fx.n1 <= 0 || rt.rb <= 0) return 0;
+  if (const char* e = getenv("GPJC_READOUT_NB")) {
+    const int v = atoi(e);
+    if (v == 0) return 0;
+    if (v >= 1 && v <= kReadoutMaxNb && readout_fwd2_smem(g, rt.rb, v) <= 227 * 1024) return v;
+  }
+  int best = 0;
+  double best_eff = -1.0;
+  for (int nb = 1; nb <= std::min(kReadoutMaxNb, g.nc); ++nb) {
+    if (readout_fwd2_smem(g, rt.rb, nb) > 112 * 1024) break;
+    const long t1 = (long)nb * rt.rb * g.os * g.fx.n2, t2 = (long)nb * rt.rb * g.os * g.fx.n1;
+    const double eff = double(t1 + t2) / (256.0 * double((t1 + 255) / 256 + (t2 + 255) / 256));
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = nb;
+    }
+  }
+  return best;
+}
+
 extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
   if (!gm || !out) return fail(GPJC_EINVAL, "null geometry or output pointer");
   *out = nullptr;
@@ -471,6 +503,7 @@ extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
       rt.hstage = hstage;
       rt.hdr = nullptr;
       rt.cols = nullptr;
+      rt.nb = adj ? 0 : pick_readout_nb(g, rt);
       if (best) {
         std::vector<int4> hdr, cols;
         build_readout_tiles(rh, best, adj != 0, ts, &hdr, &cols);
@@ -901,6 +934,7 @@ struct gpjc_op {
   float2 *vb, *vr, *vp, *vy, *vv, *vtmp;
   float2 *V, *TV;  // lazily allocated (simulation)
   void* V16;       // 16-bit hybrid data [rows][nc][ntx] of the tensor-core operator
+  bool tc_ro;      // readout stage on the tensor cores (16-bit operators, w >= 8; see tc_readout)
   CUtensorMap map16;
   double* partials;
   int npartials;
@@ -976,6 +1010,24 @@ static int auto_nchunk(const gpjc_plan* p) {
   return n;
 }
 
+// Whether a 16-bit operator runs its readout stage on the tensor cores
+// (k1_sim_* spectra + k_tc_compress / k_tc_expand) or on the FP32
+// register-tiled kernels of the FP32 operator.  Patches narrower than 8
+// samples give the compression GEMM TMA boxes of 16-32 bytes and a K of
+// nc w per group: on the 224 x 224 x 160 volume with per-period groups of
+// w = 2 the tensor-core readout ran at 0.56x the FP32 one (compression and
+// expansion kernels ~10x off their HBM traffic) while saving a contraction
+// of two taps per patch, and its spectra buffer took 12 GB.
+// GPJC_TC_READOUT=0 / 1 forces either.
+static bool tc_readout(const gpjc_plan* p, gpjc_precision prec) {
+  if (prec == GPJC_FP32) return false;
+  if (const char* e = getenv("GPJC_TC_READOUT")) {
+    if (e[0] == '0') return false;
+    if (e[0] == '1') return true;
+  }
+  return p->w >= 8;
+}
+
 // Workspace layout of an operator: chunk counts and element counts of every
 // device buffer gpjc_op_create allocates (shared with gpjc_query).
 struct OpSizes {
@@ -1015,7 +1067,7 @@ static OpSizes op_sizes(const gpjc_plan* p, gpjc_precision prec, int nchunk) {
   z.HN = (size_t)g.rows * g.ntxc;
   z.npartials = std::max(pe_normal_blocks(g, g.ntxc), sum_parts_blocks(z.L)) + 16;
   z.hist_len = (size_t)1 << 14;
-  z.spectra = prec != GPJC_FP32 ? (size_t)g.rows * g.nc * g.ntx : 0;
+  z.spectra = tc_readout(p, prec) ? (size_t)g.rows * g.nc * g.ntx : 0;
   const size_t c64 = z.HN * nmax + z.HN + z.L * (size_t)z.nchunk_a_max + 6 * z.L + (g.dim3d ? z.HN : 0) + z.spectra;
   z.bytes = sizeof(float2) * c64 + sizeof(double) * (z.npartials + SC_N + z.hist_len) + 4 * sizeof(unsigned) +
             4 * sizeof(int) + sizeof(double) * ((size_t)g.rows + 3 * (size_t)p->n_sets);
@@ -1057,6 +1109,7 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   op->plan = p;
   op->coil = (const float2*)d_coil;
   op->prec = prec;
+  op->tc_ro = tc_readout(p, prec);
   const OpSizes z = op_sizes(p, prec, nchunk);
   op->nchunk = z.nchunk;
   const int nmax = z.nchunk_max;
@@ -1088,7 +1141,7 @@ extern "C" gpjc_status gpjc_op_create(const gpjc_groups* gr, const float* d_coil
   CK(cudaMemset(op->status, 0, 4 * sizeof(int)));
   op->V = op->TV = nullptr;
   op->V16 = nullptr;
-  if (prec != GPJC_FP32) {
+  if (op->tc_ro) {
     // one buffer serves the forward spectra (FP16, or FP32 for the split BF16
     // compression) and the FP32 adjoint spectra
     float2* v16;
@@ -1169,11 +1222,12 @@ extern "C" void gpjc_op_destroy(gpjc_op* op) {
 
 // --- internal launch sequences (no validation) ---
 // readout stage of E_c into op->Hpart (register-tiled kernel when the plan has
-// tiles; 16-bit hybrid data + tensor-core compression for BF16 / FP16)
+// tiles; 16-bit hybrid data + tensor-core compression for BF16 / FP16
+// operators whose readout runs on the tensor cores)
 static cudaError_t readout_fwd(const gpjc_op* op, const float2* x, cudaStream_t st) {
   const gpjc_plan* p = op->plan;
   if (op->lb0_G) return launch_lb0_fwd(p->geo, op->lb0_G, x, op->Hpart, st);
-  if (op->prec != GPJC_FP32) {
+  if (op->tc_ro) {
     // BF16: FP32 spectra, split into head + remainder by the compression GEMM;
     // FP16: FP16 spectra, one rounding
     const int fmt = op->prec == GPJC_BF16 ? 1 : 0;
@@ -1195,15 +1249,17 @@ static cudaError_t readout_fwd(const gpjc_op* op, const float2* x, cudaStream_t 
     }
     return cudaSuccess;
   }
-  if (p->rt_f.rb && !op->legacy_readout)
+  if (p->rt_f.rb && !op->legacy_readout) {
+    if (p->rt_f.nb) return launch_k1f_batched(p->geo, p->rt_f, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st);
     return launch_k1f_tiled(p->geo, p->rt_f, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st);
+  }
   return launch_k1_fwd_fp32(p->geo, x, op->coil, op->gr->AT, op->Hpart, op->nchunk, st);
 }
 // readout stage of E_c^H from op->H2 into op->xparts
 static cudaError_t readout_adj(const gpjc_op* op, cudaStream_t st) {
   const gpjc_plan* p = op->plan;
   if (op->lb0_G) return launch_lb0_adj(p->geo, op->lb0_G, op->H2, op->xparts, op->nchunk_a, st);
-  if (op->prec != GPJC_FP32) {
+  if (op->tc_ro) {
     const int fmt = op->prec == GPJC_BF16 ? 1 : 0;
     TcGeom t = p->tc16;
     t.scale = op->gr->scale;
@@ -1234,7 +1290,7 @@ static gpjc_status op_fwd(const gpjc_op* cop, const float2* x, float2* y, cudaSt
   CK(readout_fwd(op, x, st));
   prof_end(op, st, m);
   prof_begin(op, GPJC_STAGE_PHASE_ENCODE, st, &m);
-  CK(launch_pe_fwd(g, op->Hpart, op->prec == GPJC_FP32 ? op->nchunk : 1, g.ntxc, op->T, y, st));
+  CK(launch_pe_fwd(g, op->Hpart, op->tc_ro ? 1 : op->nchunk, g.ntxc, op->T, y, st));
   prof_end(op, st, m);
   return GPJC_OK;
 }
@@ -1261,7 +1317,7 @@ static gpjc_status op_normal_parts(const gpjc_op* cop, const float2* x, double* 
   CK(readout_fwd(op, x, st));
   prof_end(op, st, m);
   prof_begin(op, GPJC_STAGE_PHASE_ENCODE, st, &m);
-  CK(launch_pe_normal(g, op->Hpart, op->prec == GPJC_FP32 ? op->nchunk : 1, g.ntxc, op->T, op->H2, op->partials,
+  CK(launch_pe_normal(g, op->Hpart, op->tc_ro ? 1 : op->nchunk, g.ntxc, op->T, op->H2, op->partials,
                       op->counter, qq, st));
   prof_end(op, st, m);
   prof_begin(op, GPJC_STAGE_READOUT_ADJ, st, &m);
@@ -1392,7 +1448,7 @@ extern "C" gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchu
   gpjc_status s = GPJC_OK;
   // adjoint chunks first (forward fixed), then forward chunks, then (16-bit
   // operators) the row pieces of the adjoint
-  const int npass = op->prec == GPJC_FP32 ? 2 : 3;
+  const int npass = op->tc_ro ? 3 : 2;
   for (int pass = 0; pass < npass && !s; ++pass) {
     int* knob = pass == 0 ? &op->nchunk_a : pass == 1 ? &op->nchunk : &op->adj_pieces;
     const int nmax = pass == 0 ? op->nchunk_a_max : pass == 1 ? op->nchunk_max : kMaxAdjPieces;

@@ -1,6 +1,7 @@
 // Device bodies of the FP32 register-tiled readout stage, shared by the
 // single-slice kernels (k_readout_f.cu, k_readout_a.cu, k_readout_a2.cu)
-// and the persistent batch kernel (k_batch.cu).
+// and the persistent batch kernel (k_batch.cu), and the forward kernel with
+// batched readout transforms (k1f_batched, k_readout_f2.cu).
 //
 // Readout stage of E_c and E_c^H, FP32, register-tiled (Eq. 13-15).
 //
@@ -86,6 +87,80 @@ __device__ __forceinline__ float2 ldm(const float2* p) {
 }
 
 // ------------------------------------------------------------------ forward --
+// A_g contraction of one coil's spectra U (rows of the block, stride st,
+// upad layout) into the register tiles: acc[m][c][k] += sum_tau
+// A_g[k][nw + tau] U[uoff + tau] (Eq. 13).
+template <int MAXT>
+__device__ __forceinline__ void k1f_contract(float2 (&acc)[MAXT][4][4], const int4 (&hdr)[MAXT],
+                                             const int (&uoff)[MAXT][4], const float2* U,
+                                             const float2* __restrict__ AT, int nw, int w) {
+#pragma unroll
+  for (int m = 0; m < MAXT; ++m) {
+    const int4 h = hdr[m];  // (aoff_g + k0, keep_g, kcnt, unused)
+    if (h.z == 0) continue;
+    const float2* Ap = AT + h.x + (size_t)nw * h.y;
+    // full tiles with 16-byte aligned rows take two 16-byte loads per tau
+    const bool vec = h.z == 4 && (h.y & 1) == 0 && (((uintptr_t)Ap) & 15) == 0;
+    // patches on 8-sample boundaries: two samples per 16-byte load of U
+    bool upair = vec && (w & 7) == 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) upair = upair && (uoff[m][c] < 0 || (uoff[m][c] & 7) == 0);
+    if (upair) {
+#pragma unroll 2
+      for (int tau = 0; tau < w; tau += 2) {
+        float2 a0[4], a1[4], u0[4], u1[4];
+        {
+          const float4 p01 = __ldg(reinterpret_cast<const float4*>(Ap));
+          const float4 p23 = __ldg(reinterpret_cast<const float4*>(Ap + 2));
+          const float4 q01 = __ldg(reinterpret_cast<const float4*>(Ap + h.y));
+          const float4 q23 = __ldg(reinterpret_cast<const float4*>(Ap + h.y + 2));
+          a0[0] = make_float2(p01.x, p01.y); a0[1] = make_float2(p01.z, p01.w);
+          a0[2] = make_float2(p23.x, p23.y); a0[3] = make_float2(p23.z, p23.w);
+          a1[0] = make_float2(q01.x, q01.y); a1[1] = make_float2(q01.z, q01.w);
+          a1[2] = make_float2(q23.x, q23.y); a1[3] = make_float2(q23.z, q23.w);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (uoff[m][c] >= 0) v = *reinterpret_cast<const float4*>(U + upad(uoff[m][c] + tau));
+          u0[c] = make_float2(v.x, v.y);
+          u1[c] = make_float2(v.z, v.w);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            cfma(acc[m][c][k], a0[k], u0[c]);
+            cfma(acc[m][c][k], a1[k], u1[c]);
+          }
+        Ap += 2 * h.y;
+      }
+      continue;
+    }
+    for (int tau = 0; tau < w; ++tau) {
+      float2 a[4], u[4];
+      if (vec) {
+        const float4 a01 = __ldg(reinterpret_cast<const float4*>(Ap));
+        const float4 a23 = __ldg(reinterpret_cast<const float4*>(Ap + 2));
+        a[0] = make_float2(a01.x, a01.y);
+        a[1] = make_float2(a01.z, a01.w);
+        a[2] = make_float2(a23.x, a23.y);
+        a[3] = make_float2(a23.z, a23.w);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) a[k] = k < h.z ? __ldg(Ap + k) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) u[c] = uoff[m][c] >= 0 ? U[upad(uoff[m][c] + tau)] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cfma(acc[m][c][k], a[k], u[c]);
+      Ap += h.y;
+    }
+  }
+}
+
 template <int MAXT, bool P>
 __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const float2* __restrict__ x,
                                          const float2* __restrict__ coil, const float2* __restrict__ AT,
@@ -159,72 +234,7 @@ __device__ __forceinline__ void k1f_body(const Geo& g, const RTiles& tl, const f
         __syncthreads();
       }
     }
-    const int nw = n * w;
-#pragma unroll
-    for (int m = 0; m < MAXT; ++m) {
-      const int4 h = hdr[m];  // (aoff_g + k0, keep_g, kcnt, unused)
-      if (h.z == 0) continue;
-      const float2* Ap = AT + h.x + (size_t)nw * h.y;
-      // full tiles with 16-byte aligned rows take two 16-byte loads per tau
-      const bool vec = h.z == 4 && (h.y & 1) == 0 && (((uintptr_t)Ap) & 15) == 0;
-      // patches on 8-sample boundaries: two samples per 16-byte load of U
-      bool upair = vec && (w & 7) == 0;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) upair = upair && (uoff[m][c] < 0 || (uoff[m][c] & 7) == 0);
-      if (upair) {
-#pragma unroll 2
-        for (int tau = 0; tau < w; tau += 2) {
-          float2 a0[4], a1[4], u0[4], u1[4];
-          {
-            const float4 p01 = __ldg(reinterpret_cast<const float4*>(Ap));
-            const float4 p23 = __ldg(reinterpret_cast<const float4*>(Ap + 2));
-            const float4 q01 = __ldg(reinterpret_cast<const float4*>(Ap + h.y));
-            const float4 q23 = __ldg(reinterpret_cast<const float4*>(Ap + h.y + 2));
-            a0[0] = make_float2(p01.x, p01.y); a0[1] = make_float2(p01.z, p01.w);
-            a0[2] = make_float2(p23.x, p23.y); a0[3] = make_float2(p23.z, p23.w);
-            a1[0] = make_float2(q01.x, q01.y); a1[1] = make_float2(q01.z, q01.w);
-            a1[2] = make_float2(q23.x, q23.y); a1[3] = make_float2(q23.z, q23.w);
-          }
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (uoff[m][c] >= 0) v = *reinterpret_cast<const float4*>(U + upad(uoff[m][c] + tau));
-            u0[c] = make_float2(v.x, v.y);
-            u1[c] = make_float2(v.z, v.w);
-          }
-#pragma unroll
-          for (int c = 0; c < 4; ++c)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              cfma(acc[m][c][k], a0[k], u0[c]);
-              cfma(acc[m][c][k], a1[k], u1[c]);
-            }
-          Ap += 2 * h.y;
-        }
-        continue;
-      }
-      for (int tau = 0; tau < w; ++tau) {
-        float2 a[4], u[4];
-        if (vec) {
-          const float4 a01 = __ldg(reinterpret_cast<const float4*>(Ap));
-          const float4 a23 = __ldg(reinterpret_cast<const float4*>(Ap + 2));
-          a[0] = make_float2(a01.x, a01.y);
-          a[1] = make_float2(a01.z, a01.w);
-          a[2] = make_float2(a23.x, a23.y);
-          a[3] = make_float2(a23.z, a23.w);
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) a[k] = k < h.z ? __ldg(Ap + k) : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c) u[c] = uoff[m][c] >= 0 ? U[upad(uoff[m][c] + tau)] : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int k = 0; k < 4; ++k) cfma(acc[m][c][k], a[k], u[c]);
-        Ap += h.y;
-      }
-    }
+    k1f_contract<MAXT>(acc, hdr, uoff, U, AT, n * w, w);
     __syncthreads();
   }
   float2* out = Hpart + ((size_t)chunk * g.rows + row0) * g.ntxc;
@@ -253,7 +263,185 @@ __global__ void __launch_bounds__(kRThreads) k1f_tiled(Geo g, RTiles tl, const f
   k1f_body<MAXT, false>(g, tl, x, coil, AT, Hpart, cpc, blockIdx.x, blockIdx.y, rsm);
 }
 
+// ------------------------------------------- forward, batched transforms --
+// Two-pass readout lengths (g.fx.n1 > 0).  Coils are taken nb at a time: the
+// os readout DFTs of every row of the block and of the nb coils run in one
+// two-pass call (nb * nrows * os transforms, so that both passes give every
+// thread a task where one row of one coil would leave most of them idle),
+// then the A_g contraction reads the nb spectra into the same register
+// tiles.  Three block barriers per nb coils: after c_n x, between the two
+// passes, after the second pass; the contraction of one step needs none
+// before the next step's c_n x, which writes a buffer the contraction does
+// not read.
+//
+// Shared memory (readout_fwd2_smem): U, nb spectra buffers of the block's
+// rows (upad layout, usz each); A, c_n x per (coil, row); B, the FFT
+// scratch (nb * rb * ntx); the twiddle table.
+__host__ __device__ inline int fwd2_usz(int rb, int ntx) { return (upad_size(rb * u_stride(ntx)) + 1) & ~1; }
+
+template <int MAXT>
+__global__ void __launch_bounds__(kRThreads) k1f_batched(Geo g, RTiles tl, const float2* __restrict__ x,
+                                                         const float2* __restrict__ coil,
+                                                         const float2* __restrict__ AT,
+                                                         float2* __restrict__ Hpart, int cpc, int nbmax) {
+  extern __shared__ float2 rsm[];
+  const int rb = tl.rb, st = u_stride(g.ntx), usz = fwd2_usz(rb, g.ntx);
+  const int nx = g.nx, os = g.os, w = g.w;
+  float2* U = rsm;
+  float2* A = U + nbmax * usz;
+  float2* B = A + nbmax * rb * nx;
+  float2* tw = B + nbmax * rb * g.ntx;
+  const int row0 = blockIdx.x * rb, chunk = blockIdx.y;
+  const int nrows = min(rb, g.rows - row0);
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = g.tw_x[i];
+  const size_t L = (size_t)g.rows * nx;
+
+  float2 acc[MAXT][4][4];
+  int4 hdr[MAXT];
+  int uoff[MAXT][4];
+#pragma unroll
+  for (int m = 0; m < MAXT; ++m) {
+    const int tile = threadIdx.x + m * kRThreads;
+    hdr[m] = tile < tl.nt ? tl.hdr[tile] : make_int4(0, 1, 0, 0);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int4 cc = tile < tl.nt ? tl.cols[tile * 4 + c] : make_int4(-1, -1, 0, 0);
+      uoff[m][c] = (cc.x >= 0 && cc.x / st < nrows) ? cc.x : -1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[m][c][k] = make_float2(0.f, 0.f);
+    }
+  }
+  const int per = nrows * os;  // transforms per coil
+  const int n0 = chunk * cpc, n1 = min(g.nc, n0 + cpc);
+  for (int n = n0; n < n1; n += nbmax) {
+    const int nb = min(nbmax, n1 - n);
+    // c_n x for the nb coils and the block's rows, [coil j][row r][x]
+    const float2* xb = x + (size_t)row0 * nx;
+    for (int i = threadIdx.x; i < nb * nrows * nx; i += blockDim.x) {
+      const int j = i / (nrows * nx), rx = i - j * nrows * nx;
+      A[i] = cmul(__ldg(coil + (size_t)(n + j) * L + (size_t)row0 * nx + rx), __ldg(xb + rx));
+    }
+    __syncthreads();
+    // transform f = (j nrows + r) os + s: pre-twiddle s while loading, the
+    // wave / centring factor of (row, t = m os + s) while storing U_j
+    auto ld = [&](int f, int xx) {
+      const int q = f / os, s = f - q * os;
+      return cmul(A[q * nx + xx], __ldg(g.pre + s * nx + xx));
+    };
+    auto stf = [&](int f, int m, float2 v) {
+      const int q = f / os, s = f - q * os, j = q / nrows, r = q - j * nrows;
+      const int t = m * os + s;
+      U[j * usz + upad(r * st + t)] = cmul(v, post_at(g, t, row0 + r));
+    };
+    fft2p_cb_dispatch<-1>(g.fx.n1, g.fx.n2, ld, stf, B, nb * per, tw, threadIdx.x, blockDim.x);
+    for (int j = 0; j < nb; ++j) k1f_contract<MAXT>(acc, hdr, uoff, U + j * usz, AT, (n + j) * w, w);
+  }
+  float2* out = Hpart + ((size_t)chunk * g.rows + row0) * g.ntxc;
+#pragma unroll
+  for (int m = 0; m < MAXT; ++m) {
+    const int tile = threadIdx.x + m * kRThreads;
+    if (tile >= tl.nt) continue;
+    const int kc = hdr[m].z;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (uoff[m][c] < 0) continue;
+      const int o = tl.cols[tile * 4 + c].y;  // r * ntxc + off_p + k0
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < kc) out[o + k] = acc[m][c][k];
+    }
+  }
+}
+
 // ------------------------------------------------------------------ adjoint --
+// A_g^H on every tile of the block for coil n (Eq. 15): U_r[t] = sum_k
+// conj(A_g[k][n w + tau]) H2[row][off_p + k], TS samples x 4 columns per
+// tile, written to U (rows of the block, stride st, spad layout): in natural
+// order t for two-pass lengths (the FFT applies the wave / centring factor
+// while loading), else times conj(post) at s nx + m for the Stockham FFT.
+template <bool P, int TS>
+__device__ __forceinline__ void k1a_contract(const Geo& g, const RTiles& tl, const float2* __restrict__ H2,
+                                             const float2* Hs, bool hs, const float2* __restrict__ Arow, int n,
+                                             int row0, int nrows, int st, float2* U) {
+  const int nx = g.nx, os = g.os, w = g.w, ns = g.ns;
+  // A^H on every tile: U_r[t] = sum_k conj(A_g[k][n w + tau]) H2[row][off_p + k]
+  // (TS samples x 4 columns per tile); the tile descriptors are re-read
+  // (L1) to keep registers for the sums
+  for (int tile = threadIdx.x; tile < tl.nt; tile += kRThreads) {
+    const int4 h = tl.hdr[tile];  // (aoff_g + tau0, keep_g, tcnt, unused)
+    int cr[4], hoff[4];
+    const float2* hp[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int4 cc = tl.cols[tile * 4 + c];  // (r, off_p, p w + tau0, 0)
+      cr[c] = (cc.x >= 0 && cc.x < nrows) ? cc.x : -1;
+      hp[c] = cr[c] >= 0 ? H2 + (size_t)(row0 + cc.x) * g.ntxc + cc.y : H2;
+      hoff[c] = cr[c] >= 0 ? cc.x * g.ntxc + cc.y : 0;
+    }
+    float2 acc[4][TS];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int k = 0; k < TS; ++k) acc[c][k] = make_float2(0.f, 0.f);
+    const float2* Ap = Arow + h.x + n * w;
+    // full tiles with 16-byte aligned rows load two samples at a time
+    const bool vec = h.z == TS && (ns & 1) == 0 && (((uintptr_t)Ap) & 15) == 0;
+#pragma unroll 2
+    for (int k = 0; k < h.y; ++k) {
+      float2 a[TS], hv[4];
+      if (vec) {
+#pragma unroll
+        for (int tt = 0; tt < TS; tt += 2) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(Ap + tt));
+          a[tt] = make_float2(v.x, v.y);
+          a[tt + 1] = make_float2(v.z, v.w);
+        }
+      } else {
+#pragma unroll
+        for (int tt = 0; tt < TS; ++tt) a[tt] = tt < h.z ? __ldg(Ap + tt) : make_float2(0.f, 0.f);
+      }
+      if (hs) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) hv[c] = cr[c] >= 0 ? Hs[hpad(hoff[c] + k)] : make_float2(0.f, 0.f);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) hv[c] = cr[c] >= 0 ? ldm<P>(hp[c] + k) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int tt = 0; tt < TS; ++tt) cfmac(acc[c][tt], a[tt], hv[c]);
+      Ap += ns;
+    }
+    const bool two = g.fx.n1 > 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (cr[c] < 0) continue;
+      float2* Ur = U + spad(cr[c] * st);
+      const int t0 = tl.cols[tile * 4 + c].z;
+      if (two) {
+        // natural order t; the FFT applies the wave / centring factor while loading
+#pragma unroll
+        for (int tt = 0; tt < TS; ++tt)
+          if (tt < h.z) Ur[spad(t0 + tt)] = acc[c][tt];
+        continue;
+      }
+      const int row = row0 + cr[c];
+      const float2* py = g.post_y + (size_t)(row % g.ny) * g.ntx;
+      const float2* pz = g.post_z + (size_t)(row / g.ny) * g.ntx;
+#pragma unroll
+      for (int tt = 0; tt < TS; ++tt) {
+        if (tt >= h.z) continue;
+        const int t = t0 + tt;
+        const int mm = t / os, s = t - mm * os;
+        float2 pt = __ldg(py + t);
+        if (g.nz > 1) pt = cmul(pt, __ldg(pz + t));
+        Ur[spad(s * nx + mm)] = cmulc(pt, acc[c][tt]);
+      }
+    }
+  }
+}
+
 template <int MAXX, bool P, int TS>
 __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const float2* __restrict__ H2,
                                          const float2* __restrict__ coil, const float2* __restrict__ Arow,
@@ -268,7 +456,7 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
   const int nrows = min(rb, g.rows - row0);
   for (int i = threadIdx.x; i < g.nx; i += blockDim.x) tw[i] = g.tw_x[i];
   const size_t L = (size_t)g.rows * g.nx;
-  const int nx = g.nx, os = g.os, w = g.w, ns = g.ns;
+  const int nx = g.nx, os = g.os;
   const bool hs = tl.hstage != 0;
   if (hs) {
     // the block's rows of H2, read once for all coils of the chunk
@@ -282,82 +470,7 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
   __syncthreads();
   const int n0 = chunk * cpc, n1 = min(g.nc, n0 + cpc);
   for (int n = n0; n < n1; ++n) {
-    // A^H on every tile: U_r[t] = sum_k conj(A_g[k][n w + tau]) H2[row][off_p + k]
-    // (TS samples x 4 columns per tile); the tile descriptors are re-read
-    // (L1) to keep registers for the sums
-    for (int tile = threadIdx.x; tile < tl.nt; tile += kRThreads) {
-      const int4 h = tl.hdr[tile];  // (aoff_g + tau0, keep_g, tcnt, unused)
-      int cr[4], hoff[4];
-      const float2* hp[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int4 cc = tl.cols[tile * 4 + c];  // (r, off_p, p w + tau0, 0)
-        cr[c] = (cc.x >= 0 && cc.x < nrows) ? cc.x : -1;
-        hp[c] = cr[c] >= 0 ? H2 + (size_t)(row0 + cc.x) * g.ntxc + cc.y : H2;
-        hoff[c] = cr[c] >= 0 ? cc.x * g.ntxc + cc.y : 0;
-      }
-      float2 acc[4][TS];
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int k = 0; k < TS; ++k) acc[c][k] = make_float2(0.f, 0.f);
-      const float2* Ap = Arow + h.x + n * w;
-      // full tiles with 16-byte aligned rows load two samples at a time
-      const bool vec = h.z == TS && (ns & 1) == 0 && (((uintptr_t)Ap) & 15) == 0;
-#pragma unroll 2
-      for (int k = 0; k < h.y; ++k) {
-        float2 a[TS], hv[4];
-        if (vec) {
-#pragma unroll
-          for (int tt = 0; tt < TS; tt += 2) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(Ap + tt));
-            a[tt] = make_float2(v.x, v.y);
-            a[tt + 1] = make_float2(v.z, v.w);
-          }
-        } else {
-#pragma unroll
-          for (int tt = 0; tt < TS; ++tt) a[tt] = tt < h.z ? __ldg(Ap + tt) : make_float2(0.f, 0.f);
-        }
-        if (hs) {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) hv[c] = cr[c] >= 0 ? Hs[hpad(hoff[c] + k)] : make_float2(0.f, 0.f);
-        } else {
-#pragma unroll
-          for (int c = 0; c < 4; ++c) hv[c] = cr[c] >= 0 ? ldm<P>(hp[c] + k) : make_float2(0.f, 0.f);
-        }
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-#pragma unroll
-          for (int tt = 0; tt < TS; ++tt) cfmac(acc[c][tt], a[tt], hv[c]);
-        Ap += ns;
-      }
-      const bool two = g.fx.n1 > 0;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (cr[c] < 0) continue;
-        float2* Ur = U + spad(cr[c] * st);
-        const int t0 = tl.cols[tile * 4 + c].z;
-        if (two) {
-          // natural order t; the FFT applies the wave / centring factor while loading
-#pragma unroll
-          for (int tt = 0; tt < TS; ++tt)
-            if (tt < h.z) Ur[spad(t0 + tt)] = acc[c][tt];
-          continue;
-        }
-        const int row = row0 + cr[c];
-        const float2* py = g.post_y + (size_t)(row % g.ny) * g.ntx;
-        const float2* pz = g.post_z + (size_t)(row / g.ny) * g.ntx;
-#pragma unroll
-        for (int tt = 0; tt < TS; ++tt) {
-          if (tt >= h.z) continue;
-          const int t = t0 + tt;
-          const int mm = t / os, s = t - mm * os;
-          float2 pt = __ldg(py + t);
-          if (g.nz > 1) pt = cmul(pt, __ldg(pz + t));
-          Ur[spad(s * nx + mm)] = cmulc(pt, acc[c][tt]);
-        }
-      }
-    }
+    k1a_contract<P, TS>(g, tl, H2, Hs, hs, Arow, n, row0, nrows, st, U);
     __syncthreads();
     for (int r = 0; r < nrows; ++r) {
       float2* Ur = U + spad(r * st);

@@ -18,6 +18,10 @@ size_t readout_adj_smem(const Geo& g, int rb, int hstage) {
          (size_t)(spad_size(rb * st) + spad_size(g.ntx) + g.nx + (hstage ? hpad_size(rb * g.ntxc) : 0));
 }
 
+size_t readout_fwd2_smem(const Geo& g, int rb, int nb) {
+  return sizeof(float2) * ((size_t)nb * fwd2_usz(rb, g.ntx) + (size_t)nb * rb * (g.nx + g.ntx) + g.nx);
+}
+
 void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, int ts, std::vector<int4>* hdr,
                          std::vector<int4>* cols) {
   const int st = u_stride(h.ntx);

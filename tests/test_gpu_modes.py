@@ -112,15 +112,23 @@ def periodic_3d():
     return wl, case, S, x_ref
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
-def test_3d_periodic_groups_end_to_end(gp, prec, periodic_3d):
+@pytest.mark.parametrize("prec,tc", [(0, None), (1, None), (2, None), (1, "1"), (2, "1")])
+def test_3d_periodic_groups_end_to_end(gp, prec, tc, periodic_3d, monkeypatch):
+    """w = 2: the 16-bit operators keep the FP32 readout kernels by default
+    (no spectra buffer in their workspace); GPJC_TC_READOUT=1 forces the
+    tensor-core readout, which must agree as well."""
     wl, case, S, x_ref = periodic_3d
     g = wl.geom
     assert (g.w, g.n_groups, g.ntx // g.w) == (2, 12, 168)
+    if tc is not None:
+        monkeypatch.setenv("GPJC_TC_READOUT", tc)
     plan = gp.Plan(g)
     c_d = to_dev(case.coils)
     grp = gp.Groups.build(plan, c_d, to_dev(case.roi, np.uint8))
+    spectra = g.ny * g.nz * g.nc * g.ntx * 8
+    ws = grp.query(prec)[1] - grp.query(0)[1]
+    assert ws == (spectra if (prec and tc == "1") else 0)
     op = gp.Operator(grp, c_d, prec)
     x, info = op.recon(gp.compress(grp, to_dev(S), prec), alg=gp.CG, iters=wl.iters)
     assert info["status"] == 0
-    check_image(to_np(x), x_ref, 1e-5 if prec == 0 else 1e-3, f"3d56r1 precision {prec}")
+    check_image(to_np(x), x_ref, 1e-5 if prec == 0 else 1e-3, f"3d56r1 precision {prec} tc {tc}")
