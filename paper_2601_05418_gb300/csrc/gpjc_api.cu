@@ -504,6 +504,18 @@ extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
       rt.hdr = nullptr;
       rt.cols = nullptr;
       rt.nb = adj ? 0 : pick_readout_nb(g, rt);
+      // paired H2 staging when every patch starts on a 16-component boundary
+      // and every group keeps an even count <= 16 (all adjoint tiles of a
+      // full column block then read their components in pairs)
+      rt.hpair = 0;
+      if (adj && hstage) {
+        bool ok = true;
+        for (size_t q = 0; q < p->pg.size() && ok; ++q) {
+          const int kq = p->keep[p->pg[q]];
+          ok = (p->poff[q] & 15) == 0 && kq <= 16 && (kq & 1) == 0;
+        }
+        rt.hpair = ok ? 1 : 0;
+      }
       if (best) {
         std::vector<int4> hdr, cols;
         build_readout_tiles(rh, best, adj != 0, ts, &hdr, &cols);

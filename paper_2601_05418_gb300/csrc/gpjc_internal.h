@@ -62,6 +62,7 @@ struct RTiles {
   int nt;
   int ts;            // adjoint: readout samples per tile (2 or 4)
   int hstage;        // adjoint: the block's rows of H2 are staged in shared memory (rb == 1)
+  int hpair;         // adjoint, staged: paired layout (hswz) read two kept components per load
   int nb;            // forward: coils per batched-transform step of k1f_batched; 0: per-row kernel
   const int4* hdr;   // [nt]
   const int4* cols;  // [nt * 4]

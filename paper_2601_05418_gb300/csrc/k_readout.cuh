@@ -64,10 +64,26 @@ __host__ __device__ inline int u_stride(int ntx) { return (ntx + 7) & ~7; }
 __host__ __device__ inline int upad(int i) { return i + 2 * (i >> 3); }
 __host__ __device__ inline int upad_size(int n) { return n + 2 * (n >> 3) + 2; }
 
-// staged H2 rows: one padding slot every 16 columns (conflict-free when the
-// tiles of a warp read columns 16 kept components apart)
+// staged H2 rows, general layout: one padding slot every 16 columns
+// (conflict-free when the tiles of a warp read columns 16 kept components
+// apart, one component at a time)
 __host__ __device__ inline int hpad(int i) { return i + (i >> 4); }
 __host__ __device__ inline int hpad_size(int n) { return n + (n >> 4) + 1; }
+
+// staged H2 rows, paired layout (RTiles::hpair: every patch offset on a
+// 16-component boundary, even keep <= 16): element i at hswz(i).  Pairs
+// (2q, 2q + 1) stay together
+// (one 16-byte load) and the pair index q is XOR-swizzled in its low three
+// bits by bits 3-5 and 10 of q: a permutation within each aligned block of 8
+// pairs, under which the tiles of a warp (4 groups x 2 column blocks whose
+// patches start 16 kept components apart, on a 32-group, keep-16 layout)
+// read pairs in 8 different bank quads.
+__host__ __device__ inline int hswz_sw(int q) { return ((q >> 3) ^ ((q >> 10) << 2)) & 7; }
+__host__ __device__ inline int hswz(int i) {
+  const int q = i >> 1;
+  return ((q ^ hswz_sw(q)) << 1) | (i & 1);
+}
+__host__ __device__ inline int hswz_size(int n) { return (n + 15) & ~15; }
 
 
 __device__ __forceinline__ float2 post_at(const Geo& g, int t, int row) {
@@ -386,8 +402,49 @@ __device__ __forceinline__ void k1a_contract(const Geo& g, const RTiles& tl, con
     const float2* Ap = Arow + h.x + n * w;
     // full tiles with 16-byte aligned rows load two samples at a time
     const bool vec = h.z == TS && (ns & 1) == 0 && (((uintptr_t)Ap) & 15) == 0;
+    // paired staging, full tiles, columns on 16-component boundaries and an
+    // even keep <= 16: the components of a column lie in one swizzle block of
+    // 8 pairs, where pair k/2 sits at hoff + (k ^ hx) (hswz), so they are read
+    // in pairs, one 16-byte load per column and pair
+    const bool sw = hs && tl.hpair;
+    bool pairs = vec && sw && h.y <= 16 && (h.y & 1) == 0;
+    int hx[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      pairs = pairs && cr[c] >= 0 && (hoff[c] & 15) == 0;
+      hx[c] = 2 * hswz_sw(hoff[c] >> 1);
+    }
+    if (pairs) {
+#pragma unroll 1
+      for (int k = 0; k < h.y; k += 2) {
+        float2 a0[TS], a1[TS], h0[4], h1[4];
+#pragma unroll
+        for (int tt = 0; tt < TS; tt += 2) {
+          const float4 v0 = __ldg(reinterpret_cast<const float4*>(Ap + tt));
+          const float4 v1 = __ldg(reinterpret_cast<const float4*>(Ap + ns + tt));
+          a0[tt] = make_float2(v0.x, v0.y);
+          a0[tt + 1] = make_float2(v0.z, v0.w);
+          a1[tt] = make_float2(v1.x, v1.y);
+          a1[tt + 1] = make_float2(v1.z, v1.w);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float4 v = *reinterpret_cast<const float4*>(Hs + hoff[c] + (k ^ hx[c]));
+          h0[c] = make_float2(v.x, v.y);
+          h1[c] = make_float2(v.z, v.w);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int tt = 0; tt < TS; ++tt) {
+            cfmac(acc[c][tt], a0[tt], h0[c]);
+            cfmac(acc[c][tt], a1[tt], h1[c]);
+          }
+        Ap += 2 * ns;
+      }
+    }
 #pragma unroll 2
-    for (int k = 0; k < h.y; ++k) {
+    for (int k = 0; !pairs && k < h.y; ++k) {
       float2 a[TS], hv[4];
       if (vec) {
 #pragma unroll
@@ -400,7 +457,10 @@ __device__ __forceinline__ void k1a_contract(const Geo& g, const RTiles& tl, con
 #pragma unroll
         for (int tt = 0; tt < TS; ++tt) a[tt] = tt < h.z ? __ldg(Ap + tt) : make_float2(0.f, 0.f);
       }
-      if (hs) {
+      if (sw) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) hv[c] = cr[c] >= 0 ? Hs[hswz(hoff[c] + k)] : make_float2(0.f, 0.f);
+      } else if (hs) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) hv[c] = cr[c] >= 0 ? Hs[hpad(hoff[c] + k)] : make_float2(0.f, 0.f);
       } else {
@@ -451,7 +511,8 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
   float2* U = rsm;
   float2* B = U + spad_size(rb * st);
   float2* tw = B + spad_size(g.ntx);
-  float2* Hs = tw + g.nx;  // staged H2 rows (tl.hstage)
+  float2* Hs = tw + g.nx;  // staged H2 rows (tl.hstage), 16-byte aligned (one spare slot)
+  if (reinterpret_cast<uintptr_t>(Hs) & 15) ++Hs;
   const int row0 = rblock * rb;
   const int nrows = min(rb, g.rows - row0);
   for (int i = threadIdx.x; i < g.nx; i += blockDim.x) tw[i] = g.tw_x[i];
@@ -461,7 +522,10 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
   if (hs) {
     // the block's rows of H2, read once for all coils of the chunk
     const float2* src = H2 + (size_t)row0 * g.ntxc;
-    for (int i = threadIdx.x; i < nrows * g.ntxc; i += blockDim.x) Hs[hpad(i)] = ldm<P>(src + i);
+    if (tl.hpair)
+      for (int i = threadIdx.x; i < nrows * g.ntxc; i += blockDim.x) Hs[hswz(i)] = ldm<P>(src + i);
+    else
+      for (int i = threadIdx.x; i < nrows * g.ntxc; i += blockDim.x) Hs[hpad(i)] = ldm<P>(src + i);
   }
 
   float2 xacc[MAXX];
@@ -520,8 +584,10 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
   }
 }
 
+// (two-sample tiles: 3 blocks per SM, whose shared memory fits beside the
+// block's staged H2 row)
 template <int MAXX, int TS>
-__global__ void __launch_bounds__(kRThreads) k1a_tiled(Geo g, RTiles tl, const float2* __restrict__ H2,
+__global__ void __launch_bounds__(kRThreads, TS == 2 ? 3 : 1) k1a_tiled(Geo g, RTiles tl, const float2* __restrict__ H2,
                                                        const float2* __restrict__ coil,
                                                        const float2* __restrict__ Arow, float2* __restrict__ xpart,
                                                        int cpc) {

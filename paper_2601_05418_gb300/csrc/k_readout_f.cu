@@ -15,7 +15,7 @@ size_t readout_fwd_smem(const Geo& g, int rb) {
 size_t readout_adj_smem(const Geo& g, int rb, int hstage) {
   const int st = u_stride(g.ntx);
   return sizeof(float2) *
-         (size_t)(spad_size(rb * st) + spad_size(g.ntx) + g.nx + (hstage ? hpad_size(rb * g.ntxc) : 0));
+         (size_t)(spad_size(rb * st) + spad_size(g.ntx) + g.nx + (hstage ? 1 + std::max(hpad_size(rb * g.ntxc), hswz_size(rb * g.ntxc)) : 0));
 }
 
 size_t readout_fwd2_smem(const Geo& g, int rb, int nb) {

@@ -55,7 +55,15 @@ def ragged_geometry():
 def geometries():
     wl = synth.workload("2d128")
     g3 = synth.workload("3d56").geom
-    return {"2d128": wl.geom, "ragged": ragged_geometry(), "3d56": g3}
+    # keep 16 on every patch (offsets on 16-component boundaries): the
+    # adjoint stages H2 in its paired layout; periodic groups (full column
+    # blocks, pair loads) and contiguous groups (one patch per group and row:
+    # column blocks with one column, the one-component loop on that layout)
+    k16 = synth.tiny_geometry(nx=64, ny=48, nz=1, nc=8, os=4, cycles=4.0, kappa_y=1.5, n_groups=8, keep=16,
+                              lines="regular", r=2)
+    k16c = synth.tiny_geometry(nx=64, ny=40, nz=1, nc=6, os=4, cycles=4.0, kappa_y=1.5, n_groups=16, keep=16,
+                               grouping="contiguous", lines="regular", r=2)
+    return {"2d128": wl.geom, "ragged": ragged_geometry(), "3d56": g3, "keep16": k16, "keep16c": k16c}
 
 
 def case_for(g, seed):
@@ -136,7 +144,7 @@ def test_simulate_matches_oracle(gp, name):
     check_close(xa, O.EH_apply(g, coils, y), 1e-5)
 
 
-@pytest.mark.parametrize("name", ["2d128", "ragged", "3d56"])
+@pytest.mark.parametrize("name", ["2d128", "ragged", "3d56", "keep16", "keep16c"])
 def test_compressed_operator_matches_oracle(gp, name):
     g = geometries()[name]
     coils, rho, roi = case_for(g, 7)
