@@ -584,10 +584,11 @@ __device__ __forceinline__ void k1a_body(const Geo& g, const RTiles& tl, const f
   }
 }
 
-// (two-sample tiles: 3 blocks per SM, whose shared memory fits beside the
-// block's staged H2 row)
+// (register budgets for 3 blocks per SM with two-sample tiles, whose shared
+// memory fits three blocks beside the staged H2 row, and 2 with four-sample
+// tiles)
 template <int MAXX, int TS>
-__global__ void __launch_bounds__(kRThreads, TS == 2 ? 3 : 1) k1a_tiled(Geo g, RTiles tl, const float2* __restrict__ H2,
+__global__ void __launch_bounds__(kRThreads, TS == 2 ? 3 : 2) k1a_tiled(Geo g, RTiles tl, const float2* __restrict__ H2,
                                                        const float2* __restrict__ coil,
                                                        const float2* __restrict__ Arow, float2* __restrict__ xpart,
                                                        int cpc) {
