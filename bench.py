@@ -159,10 +159,11 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# DRAM bytes (read + write) per launch of the adjoint readout kernel, from
-# the ncu capture summarised in profiles/k1_readout_2d256_fp32.md; to be
-# retaken whenever that kernel changes.  (The forward kernel's traffic
-# depends on the autotuned coil-chunk count, so it is not recorded.)
+# DRAM bytes (read + write) per launch of the adjoint readout kernel
+# (k1a_tiled with the paired H2 layout, adjoint chunks 8), from the ncu
+# capture summarised in profiles/k1_readout_2d256_fp32.md; to be retaken
+# whenever that kernel changes.  (The forward kernel's traffic depends on the
+# autotuned coil-chunk count, so it is not recorded.)
 DRAM_TRAFFIC = {("2d256", 2): 30536448}
 
 
