@@ -56,9 +56,10 @@ def parse():
                     help="skip the BF16 tensor-core step timed beside the FP32 one (2d256)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the 3d224 and batch64 workloads timed after the 2d256 line")
-    ap.add_argument("--profile-case", default=None, choices=["fp32", "bf16", "fp16", "lb0", "recon16"],
-                    help="profiling driver: E_c + E_c^H pairs (or the BF16 FISTA recon) of the --workload "
-                         "operator between cudaProfilerStart / Stop, for ncu --profile-from-start off")
+    ap.add_argument("--profile-case", default=None, choices=["fp32", "bf16", "fp16", "lb0", "recon16", "groups"],
+                    help="profiling driver: E_c + E_c^H pairs (or the BF16 FISTA recon, or group rebuilds) "
+                         "of the --workload operator between cudaProfilerStart / Stop, for ncu "
+                         "--profile-from-start off")
     ap.add_argument("--reps", type=int, default=3, help="pairs (or recons) of --profile-case")
     ap.add_argument("--knobs", default=None, help="--profile-case: forward chunks, adjoint chunks, adjoint pieces")
     return ap.parse_args()
@@ -980,8 +981,8 @@ def run_profile_case(args):
     g = wl.geom
     mode = args.profile_case
     if g.nz > 1:
-        if mode not in ("fp32", "bf16", "fp16"):
-            raise SystemExit("--profile-case: the 3D workloads take fp32, bf16 or fp16")
+        if mode not in ("fp32", "bf16", "fp16", "groups"):
+            raise SystemExit("--profile-case: the 3D workloads take fp32, bf16, fp16 or groups")
         rho = synth.phantom(g.nx, g.ny, g.nz)
         roi = synth.roi_mask(rho)
         coil_np = synth.coil_maps(g.nx, g.ny, g.nz, g.nc, wl.seed)
@@ -992,6 +993,17 @@ def run_profile_case(args):
     coils = torch.from_numpy(coil_np.astype(np.complex64)).to(dev)
     grp = gpjc.Groups.build(plan, coils, torch.from_numpy(roi).to(dev))
     x = torch.from_numpy(rho.astype(np.complex64)).to(dev).reshape(g.shape)
+    if mode == "groups":
+        roi_d = torch.from_numpy(roi).to(dev)
+        grp.rebuild(coils, roi_d)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.reps):
+            grp.rebuild(coils, roi_d)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_case": mode, "workload": args.workload, "reps": args.reps}), flush=True)
+        return
     if mode == "lb0":
         fields = torch.from_numpy(synth.local_b0_fields(g.nx, g.ny, 1, 3, 7).astype(np.float32)).to(dev)
         op = gpjc.Operator.local_b0(grp, coils, fields, synth.local_b0_amplitudes(g.ntx, g.cycles, 3, 8))
