@@ -279,7 +279,9 @@ void gpjc_op_destroy(gpjc_op* op);
 gpjc_status gpjc_op_create_local_b0(const gpjc_groups* groups, const float* d_coil, int32_t n_fields,
                                     const float* d_fields, const double* h_amps, gpjc_op** out);
 /* Times the readout-stage coil-chunk choices on `stream` and keeps the
- * fastest (synchronous): the adjoint's chunk count, then the forward's, and
+ * fastest (synchronous): the adjoint's chunk count, then the forward's (each
+ * among 1-6, 8, 10, 12, 16, 24, 32 within the workspace's planes, skipping
+ * counts that would leave a chunk of coils empty), and
  * for tensor-core readouts (BF16 / FP16, w >= 8) the number of row pieces (1, 2, 4, 8)
  * in which the adjoint's tensor-core expansion and inverse readout FFT run
  * (the FP32 spectra of one piece stay in L2; the results do not depend on
