@@ -64,6 +64,10 @@ struct RTiles {
   int hstage;        // adjoint: the block's rows of H2 are staged in shared memory (rb == 1)
   int hpair;         // adjoint, staged: paired layout (hswz) read two kept components per load
   int nb;            // forward: coils per batched-transform step of k1f_batched; 0: per-row kernel
+  // forward, balanced launch of k1f_batched (bal_units > 0): one wave of
+  // bal_grid blocks over bal_units (row block, coil group) units, bal_npair
+  // units per row block, partial sums in bal_planes planes
+  int bal_grid, bal_units, bal_npair, bal_planes;
   const int4* hdr;   // [nt]
   const int4* cols;  // [nt * 4]
 };

@@ -52,7 +52,8 @@ size_t readout_adj_smem(const Geo& g, int rb, int hstage);
 constexpr int kReadoutMaxNb = 4;  // coils per batched-transform step of k1f_batched
 size_t readout_fwd2_smem(const Geo& g, int rb, int nb);
 cudaError_t launch_k1f_batched(const Geo& g, const RTiles& tl, const float2* x, const float2* coil,
-                               const float2* AT, float2* Hpart, int nchunk, cudaStream_t st);
+                               const float2* AT, float2* Hpart, int nchunk, bool balanced, cudaStream_t st);
+int k1f_batched_resident(const Geo& g, const RTiles& tl);  // resident blocks on the device (0: unknown)
 cudaError_t launch_k1f_tiled(const Geo& g, const RTiles& tl, const float2* x, const float2* coil,
                              const float2* AT, float2* Hpart, int nchunk, cudaStream_t st);
 cudaError_t launch_k1a_tiled(const Geo& g, const RTiles& tl, const float2* H2, const float2* coil,

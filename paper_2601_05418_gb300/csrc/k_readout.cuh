@@ -295,11 +295,21 @@ __global__ void __launch_bounds__(kRThreads) k1f_tiled(Geo g, RTiles tl, const f
 // scratch (nb * rb * ntx); the twiddle table.
 __host__ __device__ inline int fwd2_usz(int rb, int ntx) { return (upad_size(rb * u_stride(ntx)) + 1) & ~1; }
 
+// Balanced launch (units > 0): one wave of gridDim.x blocks; the
+// (row block, coil group of nbmax coils) units, row-block-major, are split
+// into gridDim.x contiguous ranges, so every block gets the same number of
+// units to within one.  A range covers parts of several row blocks; each
+// part (segment) sums its coils into its own plane of Hpart, numbered by the
+// segment's position among the row block's segments (block boundaries
+// B_j = floor(units j / gridDim.x) inside the row block), and the row
+// block's last segment writes zeros to the planes the row block does not
+// use, so the phase-encode stage sums `planes` planes in a fixed order.
 template <int MAXT>
 __global__ void __launch_bounds__(kRThreads) k1f_batched(Geo g, RTiles tl, const float2* __restrict__ x,
                                                          const float2* __restrict__ coil,
                                                          const float2* __restrict__ AT,
-                                                         float2* __restrict__ Hpart, int cpc, int nbmax) {
+                                                         float2* __restrict__ Hpart, int cpc, int nbmax, int units,
+                                                         int npair, int planes) {
   extern __shared__ float2 rsm[];
   const int rb = tl.rb, st = u_stride(g.ntx), usz = fwd2_usz(rb, g.ntx);
   const int nx = g.nx, os = g.os, w = g.w;
@@ -307,65 +317,103 @@ __global__ void __launch_bounds__(kRThreads) k1f_batched(Geo g, RTiles tl, const
   float2* A = U + nbmax * usz;
   float2* B = A + nbmax * rb * nx;
   float2* tw = B + nbmax * rb * g.ntx;
-  const int row0 = blockIdx.x * rb, chunk = blockIdx.y;
-  const int nrows = min(rb, g.rows - row0);
   for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = g.tw_x[i];
   const size_t L = (size_t)g.rows * nx;
 
-  float2 acc[MAXT][4][4];
-  int4 hdr[MAXT];
-  int uoff[MAXT][4];
+  // rows [row0, row0 + nrows), coils [n0, n1) into plane `plane`; zeros into
+  // planes [zero0, planes)
+  auto segment = [&](int row0, int n0, int n1, int plane, int zero0) {
+    const int nrows = min(rb, g.rows - row0);
+    float2 acc[MAXT][4][4];
+    int4 hdr[MAXT];
+    int uoff[MAXT][4];
 #pragma unroll
-  for (int m = 0; m < MAXT; ++m) {
-    const int tile = threadIdx.x + m * kRThreads;
-    hdr[m] = tile < tl.nt ? tl.hdr[tile] : make_int4(0, 1, 0, 0);
+    for (int m = 0; m < MAXT; ++m) {
+      const int tile = threadIdx.x + m * kRThreads;
+      hdr[m] = tile < tl.nt ? tl.hdr[tile] : make_int4(0, 1, 0, 0);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int4 cc = tile < tl.nt ? tl.cols[tile * 4 + c] : make_int4(-1, -1, 0, 0);
-      uoff[m][c] = (cc.x >= 0 && cc.x / st < nrows) ? cc.x : -1;
+      for (int c = 0; c < 4; ++c) {
+        const int4 cc = tile < tl.nt ? tl.cols[tile * 4 + c] : make_int4(-1, -1, 0, 0);
+        uoff[m][c] = (cc.x >= 0 && cc.x / st < nrows) ? cc.x : -1;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) acc[m][c][k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < 4; ++k) acc[m][c][k] = make_float2(0.f, 0.f);
+      }
     }
-  }
-  const int per = nrows * os;  // transforms per coil
-  const int n0 = chunk * cpc, n1 = min(g.nc, n0 + cpc);
-  for (int n = n0; n < n1; n += nbmax) {
-    const int nb = min(nbmax, n1 - n);
-    // c_n x for the nb coils and the block's rows, [coil j][row r][x]
-    const float2* xb = x + (size_t)row0 * nx;
-    for (int i = threadIdx.x; i < nb * nrows * nx; i += blockDim.x) {
-      const int j = i / (nrows * nx), rx = i - j * nrows * nx;
-      A[i] = cmul(__ldg(coil + (size_t)(n + j) * L + (size_t)row0 * nx + rx), __ldg(xb + rx));
+    const int per = nrows * os;  // transforms per coil
+    for (int n = n0; n < n1; n += nbmax) {
+      const int nb = min(nbmax, n1 - n);
+      // c_n x for the nb coils and the block's rows, [coil j][row r][x]
+      const float2* xb = x + (size_t)row0 * nx;
+      for (int i = threadIdx.x; i < nb * nrows * nx; i += blockDim.x) {
+        const int j = i / (nrows * nx), rx = i - j * nrows * nx;
+        A[i] = cmul(__ldg(coil + (size_t)(n + j) * L + (size_t)row0 * nx + rx), __ldg(xb + rx));
+      }
+      __syncthreads();
+      // transform f = (j nrows + r) os + s: pre-twiddle s while loading, the
+      // wave / centring factor of (row, t = m os + s) while storing U_j
+      auto ld = [&](int f, int xx) {
+        const int q = f / os, s = f - q * os;
+        return cmul(A[q * nx + xx], __ldg(g.pre + s * nx + xx));
+      };
+      auto stf = [&](int f, int m, float2 v) {
+        const int q = f / os, s = f - q * os, j = q / nrows, r = q - j * nrows;
+        const int t = m * os + s;
+        U[j * usz + upad(r * st + t)] = cmul(v, post_at(g, t, row0 + r));
+      };
+      fft2p_cb_dispatch<-1>(g.fx.n1, g.fx.n2, ld, stf, B, nb * per, tw, threadIdx.x, blockDim.x);
+      for (int j = 0; j < nb; ++j) k1f_contract<MAXT>(acc, hdr, uoff, U + j * usz, AT, (n + j) * w, w);
     }
-    __syncthreads();
-    // transform f = (j nrows + r) os + s: pre-twiddle s while loading, the
-    // wave / centring factor of (row, t = m os + s) while storing U_j
-    auto ld = [&](int f, int xx) {
-      const int q = f / os, s = f - q * os;
-      return cmul(A[q * nx + xx], __ldg(g.pre + s * nx + xx));
-    };
-    auto stf = [&](int f, int m, float2 v) {
-      const int q = f / os, s = f - q * os, j = q / nrows, r = q - j * nrows;
-      const int t = m * os + s;
-      U[j * usz + upad(r * st + t)] = cmul(v, post_at(g, t, row0 + r));
-    };
-    fft2p_cb_dispatch<-1>(g.fx.n1, g.fx.n2, ld, stf, B, nb * per, tw, threadIdx.x, blockDim.x);
-    for (int j = 0; j < nb; ++j) k1f_contract<MAXT>(acc, hdr, uoff, U + j * usz, AT, (n + j) * w, w);
-  }
-  float2* out = Hpart + ((size_t)chunk * g.rows + row0) * g.ntxc;
 #pragma unroll
-  for (int m = 0; m < MAXT; ++m) {
-    const int tile = threadIdx.x + m * kRThreads;
-    if (tile >= tl.nt) continue;
-    const int kc = hdr[m].z;
+    for (int m = 0; m < MAXT; ++m) {
+      const int tile = threadIdx.x + m * kRThreads;
+      if (tile >= tl.nt) continue;
+      const int kc = hdr[m].z;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      if (uoff[m][c] < 0) continue;
-      const int o = tl.cols[tile * 4 + c].y;  // r * ntxc + off_p + k0
+      for (int c = 0; c < 4; ++c) {
+        if (uoff[m][c] < 0) continue;
+        const int o = tl.cols[tile * 4 + c].y;  // r * ntxc + off_p + k0
+        float2* out = Hpart + ((size_t)plane * g.rows + row0) * g.ntxc + o;
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k < kc) out[o + k] = acc[m][c][k];
+        for (int k = 0; k < 4; ++k)
+          if (k < kc) out[k] = acc[m][c][k];
+        for (int q = zero0; q < planes; ++q) {
+          float2* z = Hpart + ((size_t)q * g.rows + row0) * g.ntxc + o;
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (k < kc) z[k] = make_float2(0.f, 0.f);
+        }
+      }
     }
+  };
+
+  // one segment per block for the row-block x coil-chunk grid (units == 0)
+  const long long G = gridDim.x, Uu = units > 0 ? units : 1;
+  int u = units > 0 ? (int)(Uu * blockIdx.x / G) : 0;
+  const int u1 = units > 0 ? (int)(Uu * (blockIdx.x + 1) / G) : 1;
+  // boundaries B_j = floor(units j / G) at or below v: ceil((v + 1) G / units)
+  auto cnt = [&](int v) { return (int)(((long long)(v + 1) * G + Uu - 1) / Uu); };
+  while (u < u1) {
+    int row0, n0, n1, plane, zero0, unext;
+    if (units == 0) {
+      row0 = blockIdx.x * rb;
+      n0 = blockIdx.y * cpc;
+      n1 = min(g.nc, n0 + cpc);
+      plane = blockIdx.y;
+      zero0 = planes;
+      unext = u1;
+    } else {
+      const int rbk = u / npair;
+      const int rs = rbk * npair, re = rs + npair;
+      unext = min(u1, re);
+      const int ord = cnt(u) - cnt(rs), nseg = 1 + cnt(re - 1) - cnt(rs);
+      row0 = rbk * rb;
+      n0 = (u - rs) * nbmax;
+      n1 = min(g.nc, (unext - rs) * nbmax);
+      plane = ord;
+      zero0 = ord == nseg - 1 ? nseg : planes;
+    }
+    segment(row0, n0, n1, plane, zero0);
+    u = unext;
   }
 }
 

@@ -169,6 +169,29 @@ def test_compressed_operator_matches_oracle(gp, name):
     assert abs(qq.item() - np.vdot(y_ref, y_ref).real) < 1e-5 * np.vdot(y_ref, y_ref).real
 
 
+@pytest.mark.parametrize("balance", ["1", "0"])
+def test_balanced_forward_readout_matches_oracle(gp, balance, monkeypatch):
+    """192 rows x 4 groups of 4 coils: 768 (row, coil group) units, enough
+    for every resident block of the device to take at least two, so the
+    forward readout runs its one-wave balanced launch (rows cut between
+    blocks sum into up to three planes); GPJC_READOUT_BALANCE=0 keeps the
+    row x coil-chunk grid.  Both against the oracle."""
+    monkeypatch.setenv("GPJC_READOUT_BALANCE", balance)
+    g = synth.tiny_geometry(nx=128, ny=192, nz=1, nc=16, os=4, cycles=4.0, kappa_y=1.5, n_groups=8, keep=12,
+                            lines="regular", r=3)
+    coils, rho, roi = case_for(g, 41)
+    As, _, _ = O.build_groups(g, coils, roi)
+    plan = gp.Plan(g)
+    op = gp.Operator(gp.Groups.from_matrices(plan, As), to_dev(coils))
+    x = synth.complex_normal(g.shape, 42)
+    y_ref = O.Ec_apply(g, coils, As, x)
+    check_close(to_np(op.E(to_dev(x))), y_ref, 1e-5)
+    qq = torch.zeros(1, dtype=torch.float64, device=DEV)
+    n = to_np(op.normal(to_dev(x), qq=qq))
+    check_close(n, O.EcH_apply(g, coils, As, y_ref), 1e-5)
+    assert abs(qq.item() - np.vdot(y_ref, y_ref).real) < 1e-5 * np.vdot(y_ref, y_ref).real
+
+
 @pytest.mark.parametrize("nchunk", [1, 2, 3, 8])
 def test_coil_chunking_is_exact(gp, nchunk):
     g = geometries()["2d128"]
