@@ -161,11 +161,11 @@ def peaks():
 
 
 # DRAM bytes (read + write) per launch of the adjoint readout kernel
-# (k1a_tiled with the paired H2 layout, adjoint chunks 8), from the ncu
+# (k1a_tiled with the paired H2 layout, adjoint chunks 6), from the ncu
 # capture summarised in profiles/k1_readout_2d256_fp32.md; to be retaken
-# whenever that kernel changes.  (The forward kernel's traffic depends on the
-# autotuned coil-chunk count, so it is not recorded.)
-DRAM_TRAFFIC = {("2d256", 2): 30536448}
+# whenever that kernel changes.  (The forward kernel's traffic depends on its
+# launch mode, so it is not recorded.)
+DRAM_TRAFFIC = {("2d256", 2): 30543872}
 
 
 def k1_flops(g, ntxc, keep_avg, contraction=True):
