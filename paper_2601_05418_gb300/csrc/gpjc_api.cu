@@ -510,16 +510,37 @@ extern "C" gpjc_status gpjc_plan_create(const gpjc_geom* gm, gpjc_plan** out) {
         ts = readout_tile_count(rh, 1, true, 4) >= 256 ? 4 : 2;
         if ((readout_tile_count(rh, 1, true, ts) + 255) / 256 > 4) best = 0;
       }
+      auto fits = [&](int rb) {
+        const int nt = readout_tile_count(rh, rb, adj != 0, 4);
+        const size_t smem = adj ? readout_adj_smem(g, rb, 0) : readout_fwd_smem(g, rb);
+        if (smem > 110 * 1024 || (nt + 255) / 256 > (adj ? 4 : 3) || rb > g.rows) return false;
+        return !(adj && (rb * nx + 255) / 256 > 8);
+      };
       if (!best) {
         ts = 4;
         hstage = 0;
         for (int rb = 1; rb <= 8; rb *= 2) {
-          const int nt = readout_tile_count(rh, rb, adj != 0, 4);
-          const size_t smem = adj ? readout_adj_smem(g, rb, 0) : readout_fwd_smem(g, rb);
-          if (smem > 110 * 1024 || (nt + 255) / 256 > (adj ? 4 : 3) || rb > g.rows) break;
-          if (adj && (rb * nx + 255) / 256 > 8) break;
+          if (!fits(rb)) break;
           best = rb;
-          if (nt >= 256) break;
+          if (readout_tile_count(rh, rb, adj != 0, 4) >= 256) break;
+        }
+      }
+      // groups with fewer than 4 patches per row (contiguous readout
+      // subregions: one) leave most of each 4-column tile empty at one row
+      // per block; more rows per block fill the columns (the 224 x 224 x 160
+      // volume's 48 contiguous groups: 25% of the contraction's multiply-adds
+      // did work at one row, 100% at four)
+      if (best && readout_col_fill(rh, best, adj != 0, ts) < 0.75) {
+        double f_best = readout_col_fill(rh, best, adj != 0, ts);
+        for (int rb = best * 2; rb <= 8; rb *= 2) {
+          if (!fits(rb)) break;
+          const double f = readout_col_fill(rh, rb, adj != 0, 4);
+          if (f > f_best + 1e-9) {
+            f_best = f;
+            best = rb;
+            ts = 4;
+            hstage = 0;
+          }
         }
       }
       RTiles& rt = adj ? p->rt_a : p->rt_f;

@@ -46,6 +46,9 @@ struct ReadoutGeomHost {
 };
 void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, int ts, std::vector<int4>* hdr,
                          std::vector<int4>* cols);
+// share of the register tiles' patch columns that hold a column (tiles of 4
+// columns over rb rows x the group's patches per row), weighted by the tiles
+double readout_col_fill(const ReadoutGeomHost& h, int rb, bool adjoint, int ts);
 int readout_tile_count(const ReadoutGeomHost& h, int rb, bool adjoint, int ts);
 size_t readout_fwd_smem(const Geo& g, int rb);
 size_t readout_adj_smem(const Geo& g, int rb, int hstage);

@@ -54,6 +54,18 @@ void build_readout_tiles(const ReadoutGeomHost& h, int rb, bool adjoint, int ts,
   }
 }
 
+double readout_col_fill(const ReadoutGeomHost& h, int rb, bool adjoint, int ts) {
+  std::vector<int> occ(h.G, 0);
+  for (int p = 0; p < (int)h.pg.size(); ++p) ++occ[h.pg[p]];
+  double useful = 0.0, total = 0.0;
+  for (int g = 0; g < h.G; ++g) {
+    const int kb = ceil_div(adjoint ? h.w : h.keep[g], adjoint ? ts : 4);
+    useful += (double)kb * rb * occ[g];
+    total += (double)kb * 4 * ceil_div(rb * occ[g], 4);
+  }
+  return total > 0.0 ? useful / total : 1.0;
+}
+
 int readout_tile_count(const ReadoutGeomHost& h, int rb, bool adjoint, int ts) {
   std::vector<std::vector<int>> occ(h.G);
   for (int p = 0; p < (int)h.pg.size(); ++p) occ[h.pg[p]].push_back(p);
