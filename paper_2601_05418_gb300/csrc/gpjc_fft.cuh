@@ -170,9 +170,9 @@ __device__ __forceinline__ void fft2p(float2* a, float2* b, int batch, int bs, c
 // element i of transform f, st(f, k, v) receives element k (pre- and
 // post-multiplications fuse into the two passes).  `b` holds batch * n
 // scratch values; ends with __syncthreads().
-template <int N1, int N2, int SIGN, typename LD>
-__device__ __forceinline__ void fft2p_pass1(LD& ld, float2* b, int batch, const float2* __restrict__ tw2, int tid,
-                                            int nthr) {
+template <int N1, int N2, int SIGN, typename LD, typename ST>
+__device__ __forceinline__ void fft2p_cb(LD& ld, ST& st, float2* b, int batch, const float2* __restrict__ tw2,
+                                         int tid, int nthr) {
   constexpr int n = N1 * N2;
   for (int task = tid; task < batch * N2; task += nthr) {
     const int f = task / N2, i2 = task - f * N2;
@@ -193,13 +193,6 @@ __device__ __forceinline__ void fft2p_pass1(LD& ld, float2* b, int batch, const 
       col[k1 ^ sw] = x;
     }
   }
-}
-
-template <int N1, int N2, int SIGN, typename LD, typename ST>
-__device__ __forceinline__ void fft2p_cb(LD& ld, ST& st, float2* b, int batch, const float2* __restrict__ tw2,
-                                         int tid, int nthr) {
-  constexpr int n = N1 * N2;
-  fft2p_pass1<N1, N2, SIGN>(ld, b, batch, tw2, tid, nthr);
   __syncthreads();
   for (int task = tid; task < batch * N1; task += nthr) {
     const int f = task / N1, k1 = task - f * N1;
