@@ -24,7 +24,7 @@
 using namespace gpjc;
 
 static constexpr int kVecChunkHost = 2048;  // vector elements per batch work item (k_readout.cu)
-static constexpr int kPeCBHost = 16;
+static constexpr int kPeCBHost = 8;  // columns per phase-encode block (kPeCB)
 
 // ------------------------------------------------------------------ launches --
 #include <atomic>

@@ -290,7 +290,7 @@ __device__ __forceinline__ bool grid_sum_finalize(double v, double* partials, un
 // ------------------------------------------------------------------ phase-encode (2D) --
 // A block owns kPeCB columns of the hybrid matrix [ny][ncols].  Centred
 // unitary DFT along y: F[ky,y] = (-1)^y (-1)^{ky + ny/2} e^{-2 pi i ky y/ny} / sqrt(ny).
-constexpr int kPeCB = 16;
+constexpr int kPeCB = 8;  // equal to kCB of k_pe.cu
 __device__ __forceinline__ float pe_sgn(int k) { return (k & 1) ? -1.0f : 1.0f; }
 
 // H = F_y^H M^T Sc for the columns of block `cb`.

@@ -12,7 +12,7 @@
 // applies A_g with FFMA as each coil's spectrum becomes available, so the
 // uncompressed hybrid data never leaves the SM.
 //
-// Phase-encode stage ("k2"): one block per 16-column slab of the hybrid
+// Phase-encode stage ("k2"): one block per 8-column slab of the hybrid
 // matrix H[row][col]; FFT along y (and z in 3D), gather / scatter of the
 // sampled lines, and for E_c^H E_c the fused mask-projection with the
 // squared norm ||E_c p||^2 accumulated for CG.
