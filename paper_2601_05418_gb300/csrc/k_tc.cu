@@ -275,8 +275,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
   unsigned char* stg = tsm;                                   // staging [lt][ncc][n_occ][box0]
   uint16_t* At = (uint16_t*)(tsm + t.stg_bytes);              // 128 x Kc core image (head)
   uint16_t* Al = At + (NI - 1) * 128 * t.Kc;                  // 128 x Kc remainder (BF16)
-  uint16_t* Bt = Al + 128 * t.Kc;                             // npad x Kc core image(s) of A_g
-  uint64_t* bars = (uint64_t*)(Bt + (size_t)NI * t.npad * t.Kc);  // [0] load, [1] mma
+  uint16_t* Bt0 = Al + 128 * t.Kc;                            // npad x Kc core image(s) of A_g, two buffers
+  const size_t bsz = (size_t)NI * t.npad * t.Kc;
+  uint64_t* bars = (uint64_t*)(Bt0 + 2 * bsz);                // [0] load, [1] mma
   uint32_t* tmem_slot = (uint32_t*)(bars + 2);
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
@@ -295,20 +296,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
   const uint32_t bbytes = (uint32_t)(NI * t.npad * t.Kc * 2);
   uint32_t ph_ld = 0, ph_mma = 0;
   bool ok = true;
-  uint64_t* stuck = nullptr;
   const int m = tid;  // A row = output column (line l, occurrence q); rows >= lt n_occ are padding
   const bool mrow = m < t.lt * t.n_occ;
   const int l = mrow ? m / t.n_occ : 0, q = mrow ? m - (m / t.n_occ) * t.n_occ : 0;
+  // Chunk c + 1's staging and A_g image are loaded while chunk c's MMAs run:
+  // its staging load is issued once the block has converted chunk c's
+  // staging (block barrier), into the same buffer; its A_g image goes to the
+  // other of two buffers, which chunk c - 1's MMAs (waited for) no longer
+  // read.  The images of chunk c + 1 are written only after chunk c's MMAs
+  // have completed.
+  bool ld_pending = false, mma_pending = false;
+  if (tid == 0) {
+    mbar_expect_tx(&bars[0], (uint32_t)t.stg_tx + bbytes);
+    tma_load_4d(stg, &tmap, x0, 0, 0, l0, &bars[0]);
+    bulk_g2s(Bt0, Bpk + (size_t)g * t.nchunks * bsz, bbytes, &bars[0]);
+  }
+  ld_pending = true;
   for (int c = 0; c < t.nchunks && ok; ++c) {
-    if (tid == 0) {
-      mbar_expect_tx(&bars[0], (uint32_t)t.stg_tx + bbytes);
-      tma_load_4d(stg, &tmap, x0, 0, c * t.ncc, l0, &bars[0]);
-      bulk_g2s(Bt, Bpk + ((size_t)g * t.nchunks + c) * NI * t.npad * t.Kc, bbytes, &bars[0]);
-    }
-    if (!(ok = block_wait(&bars[0], ph_ld))) {
-      stuck = &bars[0];
-      break;
-    }
+    uint16_t* Bt = Bt0 + (size_t)(c & 1) * bsz;
+    if (!(ok = block_wait(&bars[0], ph_ld))) break;
+    ld_pending = false;
     // staging -> 16-bit core image (row m holds its column's samples of the chunk)
     for (int nl = 0; nl < t.ncc && mrow; ++nl) {
       const size_t base = ((size_t)(l * t.ncc + nl) * t.n_occ + q) * t.box0 + shift;
@@ -337,6 +344,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
+    if (c + 1 < t.nchunks) {
+      if (tid == 0) {
+        mbar_expect_tx(&bars[0], (uint32_t)t.stg_tx + bbytes);
+        tma_load_4d(stg, &tmap, x0, 0, (c + 1) * t.ncc, l0, &bars[0]);
+        bulk_g2s(Bt0 + (size_t)((c + 1) & 1) * bsz, Bpk + ((size_t)g * t.nchunks + c + 1) * bsz, bbytes,
+                 &bars[0]);
+      }
+      ld_pending = true;
+    }
     if (tid == 0) {
       tc_fence_after();
       const uint32_t sbo = (uint32_t)(t.Kc / 8) * 128;
@@ -352,12 +368,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_tc_compress(const __grid_cons
       }
       mma_commit(&bars[1]);
     }
-    if (!(ok = block_wait(&bars[1], ph_mma))) stuck = &bars[1];
+    mma_pending = true;
+    if (!(ok = block_wait(&bars[1], ph_mma))) break;
+    mma_pending = false;
   }
   if (!ok) {
     if (tid == 0) atomicExch(status, (int)kDevTimeout);
-    // drain the operation still in flight before releasing the memory
-    mbar_wait(stuck, stuck == &bars[0] ? ph_ld : ph_mma);
+    // drain the operations still in flight before releasing the memory
+    if (ld_pending) mbar_wait(&bars[0], ph_ld);
+    if (mma_pending) mbar_wait(&bars[1], ph_mma);
   } else {
     tc_fence_after();
     // epilogue: lane m of TMEM holds column m; 8 fp32 columns = 4 complex values per load
@@ -538,7 +557,8 @@ bool make_tc_tmap(const TcGeom& t, const void* base, int lines, int ebytes, CUte
 
 size_t tc_compress_smem(const TcGeom& t, int fmt) {
   const int ni = tc_images(fmt);
-  return (size_t)t.stg_bytes + (size_t)ni * 128 * t.Kc * 2 + (size_t)ni * t.npad * t.Kc * 2 + 64;
+  // staging, the chunk's 16-bit images, two buffers of A_g images, barriers
+  return (size_t)t.stg_bytes + (size_t)ni * 128 * t.Kc * 2 + (size_t)2 * ni * t.npad * t.Kc * 2 + 64;
 }
 size_t tc_expand_smem(const TcGeom& t, int fmt) {
   return (size_t)2 * 128 * t.Kx * 2 + (size_t)tc_images(fmt) * 256 * t.Kx * 2 + 64;
