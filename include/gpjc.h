@@ -289,7 +289,11 @@ gpjc_status gpjc_op_create_local_b0(const gpjc_groups* groups, const float* d_co
 gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchunk);
 /* The operator's current launch knobs (set at creation or by
  * gpjc_op_autotune): coil chunks of the forward and of the adjoint readout
- * stage, row pieces of the 16-bit adjoint.  Any output may be NULL. */
+ * stage, row pieces of the 16-bit adjoint.  Where the FP32 forward readout
+ * runs its balanced one-wave launch (plans whose row blocks make fewer than
+ * four waves of the device's resident blocks, e.g. a 256 x 256 slice), the
+ * forward chunk count is kept but has no effect (the autotuner skips it).
+ * Any output may be NULL. */
 gpjc_status gpjc_op_tuning(const gpjc_op* op, int32_t* nchunk, int32_t* nchunk_adj, int32_t* adj_pieces);
 /* Sets those knobs (e.g. from a persisted autotuning result): nchunk in
  * [1, the forward workspace's planes], nchunk_adj in [1, the adjoint's],
