@@ -19,9 +19,10 @@
  *   P_g = U_g F_g U_g^H  (Eq. 8),  A_g = C_g U_g^H (T (x) I_w)  (Eq. 12),
  *   S'_{l,p} = A_{g(p)} s_{l,p}  (Eq. 13),  E_c = A E  (Eq. 14-15),
  *   compressed readout length N'_tx = sum_p keep[g(p)].
- * Reconstruction (Sec. 3.4): CG on E_c^H E_c x = E_c^H S' (Eq. 16) and FISTA
- *   with an orthonormal Haar l1 term on the detail bands (Eq. 17 with
- *   lambda_TV = 0).
+ * Reconstruction (Sec. 3.4): CG on E_c^H E_c x = E_c^H S' (Eq. 16), the
+ *   decoupled least squares of algorithm #1 (one CG per aliased set of rows),
+ *   and FISTA with an orthonormal Haar l1 term on the detail bands plus an
+ *   optional smoothed isotropic TV term (Eq. 17).
  *
  * Conventions for every call:
  *   - complex data are interleaved float pairs (complex64, `float` re, im);
