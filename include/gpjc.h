@@ -283,7 +283,7 @@ gpjc_status gpjc_op_create_local_b0(const gpjc_groups* groups, const float* d_co
  * fastest (synchronous): the adjoint's chunk count, then the forward's (each
  * among 1-6, 8, 10, 12, 16, 24, 32 within the workspace's planes, skipping
  * counts that would leave a chunk of coils empty), and
- * for tensor-core readouts (BF16 / FP16, w >= 8) the number of row pieces (1, 2, 4, 8)
+ * for tensor-core readouts (BF16 / FP16, w >= 8) the number of row pieces (1-8)
  * in which the adjoint's tensor-core expansion and inverse readout FFT run
  * (the FP32 spectra of one piece stay in L2; the results do not depend on
  * the split).  *nchunk receives the forward chunk count (may be NULL). */

@@ -1536,11 +1536,11 @@ extern "C" gpjc_status gpjc_op_autotune(gpjc_op* op, void* stream, int32_t* nchu
     // blocks, and a count that fills the last wave of resident blocks better
     // can win (2d256 adjoint: 6 chunks 188 us, 8 chunks 197 us); chunk counts
     // that would leave a chunk empty are skipped
-    static const int kCand[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 16, 24, 32};
+    static const int kCand[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 24, 32};
     for (int ci = 0; ci < (int)(sizeof(kCand) / sizeof(kCand[0])) && !s; ++ci) {
       const int n = kCand[ci];
       if (n > nmax) break;
-      if (pass == 2 && (n & (n - 1))) continue;  // row pieces: 1, 2, 4, 8
+      if (pass < 2 && n == 7) continue;  // chunk counts: 1-6, 8, 10, ...; row pieces: 1-8
       if (pass < 2) {
         const int cpc = (op->plan->nc + n - 1) / n;
         if ((n - 1) * cpc >= op->plan->nc) continue;
